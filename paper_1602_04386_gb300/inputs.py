@@ -1,0 +1,195 @@
+"""Seeded synthetic graph generators shared by the tests, the bench and the oracle checks.
+
+This module holds no arithmetic of the solver: it only produces symmetric CSR
+adjacency matrices (int32 row pointers, int32 column indices sorted ascending
+within each row, positive weights) from counter-based random streams, so that
+the CUDA path and the CPU oracle can be fed the same inputs.
+
+Random numbers come from the splitmix64 generator (S. Vigna, public-domain
+reference ``splitmix64.c``): output k (k = 0, 1, ...) of the stream seeded with
+``s`` is ``mix64(s + (k + 1) * 0x9E3779B97F4A7C15)``.  A uniform draw in [0, 1)
+is ``(output >> 11) * 2**-53``.  Every weight is rounded to float32 so that the
+FP32 and FP64 forms of the solver see the same graph.
+
+Workload shapes (the recipe is restated in the design doc):
+  * unit 2-D 5-point grids (vertex index r*k + c, r < m, c < k);
+  * weighted 2-D grids, edges enumerated horizontal (row-major) then vertical,
+    weight_e = f32(0.5 + u_e), u_e the e-th uniform draw of the seed's stream;
+  * small closed-form families (path, cycle, complete, star) for pins;
+  * random sparse graphs for dense-eigensolver pins.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+#: Base seed of the synthetic workloads; config c uses BASE_SEED + c.
+BASE_SEED = 20160214
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = z.astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def splitmix64(seed: int, k) -> np.ndarray:
+    """Outputs k (array) of the splitmix64 stream seeded with ``seed``."""
+    k = np.asarray(k, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        state = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (k + np.uint64(1)) * GAMMA
+    return _mix64(state)
+
+
+def uniform01(seed: int, k) -> np.ndarray:
+    """Uniform doubles in [0, 1) from outputs k of the seed's stream."""
+    return (splitmix64(seed, k) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+class CSR:
+    """Symmetric adjacency matrix in CSR form (no diagonal unless added on purpose)."""
+
+    __slots__ = ("n", "rowptr", "col", "w", "name")
+
+    def __init__(self, n, rowptr, col, w, name=""):
+        self.n = int(n)
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.w = np.ascontiguousarray(w)
+        self.name = name
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def with_dtype(self, dtype) -> "CSR":
+        return CSR(self.n, self.rowptr, self.col, self.w.astype(dtype), self.name)
+
+    def dense(self) -> np.ndarray:
+        a = np.zeros((self.n, self.n), dtype=np.float64)
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        a[rows, self.col] = self.w
+        return a
+
+    def __repr__(self):
+        return f"CSR({self.name or '?'}, n={self.n}, nnz={self.nnz}, w={self.w.dtype})"
+
+
+def csr_from_edges(n, u, v, w, dtype=np.float32, name="") -> CSR:
+    """Symmetric CSR from undirected edge lists (each edge listed once, u != v,
+    no duplicates).  Columns end up sorted ascending within every row."""
+    u = np.asarray(u, dtype=np.int64)
+    v = np.asarray(v, dtype=np.int64)
+    w = np.asarray(w, dtype=dtype)
+    rows = np.concatenate([u, v])
+    cols = np.concatenate([v, u])
+    vals = np.concatenate([w, w])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return CSR(n, rowptr.astype(np.int32), cols.astype(np.int32), vals, name)
+
+
+def grid_edges(m: int, k: int):
+    """Edges of the m x k 5-point grid, horizontal (row-major) first, then vertical."""
+    r, c = np.meshgrid(np.arange(m, dtype=np.int64), np.arange(k - 1, dtype=np.int64), indexing="ij")
+    hu = (r * k + c).ravel()
+    hv = hu + 1
+    r, c = np.meshgrid(np.arange(m - 1, dtype=np.int64), np.arange(k, dtype=np.int64), indexing="ij")
+    vu = (r * k + c).ravel()
+    vv = vu + k
+    return np.concatenate([hu, vu]), np.concatenate([hv, vv])
+
+
+def grid(m: int, k: int, weights: str = "unit", seed: int = BASE_SEED, dtype=np.float32) -> CSR:
+    """m x k 5-point grid graph; ``weights`` is "unit" or "uniform" (0.5 + U[0,1), rounded to f32)."""
+    u, v = grid_edges(m, k)
+    if weights == "unit":
+        w = np.ones(u.shape[0], dtype=np.float32)
+    elif weights == "uniform":
+        w = (0.5 + uniform01(seed, np.arange(u.shape[0]))).astype(np.float32)
+    else:
+        raise ValueError(weights)
+    return csr_from_edges(m * k, u, v, w.astype(dtype), dtype=dtype, name=f"grid{m}x{k}-{weights}")
+
+
+def path(n: int, dtype=np.float32) -> CSR:
+    u = np.arange(n - 1)
+    return csr_from_edges(n, u, u + 1, np.ones(n - 1), dtype=dtype, name=f"path{n}")
+
+
+def cycle(n: int, dtype=np.float32) -> CSR:
+    u = np.arange(n)
+    v = (u + 1) % n
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    return csr_from_edges(n, lo, hi, np.ones(n), dtype=dtype, name=f"cycle{n}")
+
+
+def complete(n: int, dtype=np.float32) -> CSR:
+    iu, ju = np.triu_indices(n, 1)
+    return csr_from_edges(n, iu, ju, np.ones(iu.shape[0]), dtype=dtype, name=f"K{n}")
+
+
+def star(n: int, dtype=np.float32) -> CSR:
+    """Vertex 0 joined to vertices 1..n-1."""
+    v = np.arange(1, n)
+    return csr_from_edges(n, np.zeros(n - 1, dtype=np.int64), v, np.ones(n - 1), dtype=dtype, name=f"star{n}")
+
+
+def random_connected(n: int, avg_deg: float, seed: int, wlo=0.1, whi=1.0, dtype=np.float32) -> CSR:
+    """Random sparse connected graph: a random spanning tree plus random extra edges,
+    weights uniform in [wlo, whi) rounded to f32."""
+    k = 0
+    perm = np.argsort(uniform01(seed, np.arange(n)), kind="stable")
+    k += n
+    # tree: perm[i] attaches to perm[j], j uniform in [0, i)
+    j = (uniform01(seed, k + np.arange(1, n)) * np.arange(1, n)).astype(np.int64)
+    k += n
+    tu, tv = perm[1:], perm[j]
+    m_extra = max(0, int(n * avg_deg / 2) - (n - 1))
+    eu = (uniform01(seed, k + np.arange(m_extra)) * n).astype(np.int64)
+    k += m_extra
+    ev = (uniform01(seed, k + np.arange(m_extra)) * n).astype(np.int64)
+    k += m_extra
+    u = np.concatenate([tu, eu])
+    v = np.concatenate([tv, ev])
+    keep = u != v
+    lo, hi = np.minimum(u[keep], v[keep]), np.maximum(u[keep], v[keep])
+    key = np.unique(lo * n + hi)
+    lo, hi = key // n, key % n
+    w = (wlo + (whi - wlo) * uniform01(seed, k + np.arange(lo.shape[0]))).astype(np.float32)
+    return csr_from_edges(n, lo, hi, w.astype(dtype), dtype=dtype, name=f"rand{n}-s{seed}")
+
+
+def disjoint_union(a: CSR, b: CSR) -> CSR:
+    """Block-diagonal union of two graphs (b's vertices shifted by a.n)."""
+    rowptr = np.concatenate([a.rowptr[:-1], b.rowptr + a.nnz]).astype(np.int32)
+    col = np.concatenate([a.col, b.col + a.n]).astype(np.int32)
+    w = np.concatenate([a.w, b.w.astype(a.w.dtype)])
+    return CSR(a.n + b.n, rowptr, col, w, name=f"{a.name}+{b.name}")
+
+
+def with_self_loops(g: CSR, rows, weight=1.0) -> CSR:
+    """Copy of g with a diagonal entry added on the given rows (self-loops)."""
+    rows = set(int(r) for r in rows)
+    rp = [0]
+    cols, ws = [], []
+    for i in range(g.n):
+        cs = list(g.col[g.rowptr[i]:g.rowptr[i + 1]])
+        vs = list(g.w[g.rowptr[i]:g.rowptr[i + 1]])
+        if i in rows:
+            pos = int(np.searchsorted(np.asarray(cs, dtype=np.int64), i))
+            cs.insert(pos, i)
+            vs.insert(pos, weight)
+        cols += cs
+        ws += vs
+        rp.append(len(cols))
+    return CSR(g.n, np.asarray(rp), np.asarray(cols), np.asarray(ws, dtype=g.w.dtype), name=g.name + "+loops")
