@@ -1,0 +1,206 @@
+/*
+ * fiedler.h -- C-ABI of the GB300 cascadic multigrid Fiedler-vector solver.
+ *
+ * The library computes the second smallest eigenpair (lambda_2, phi_2) of a
+ * weighted graph Laplacian (Def 2.1 and Def 2.2 of S. Gandhi, "Improvement of
+ * the Cascadic Multigrid Algorithm with a Gauss Seidel Smoother to Efficiently
+ * Compute the Fiedler Vector of a Graph Laplacian", 2015) with the method of
+ * its Alg. 3: heavy edge coarsening (Alg. 1) into a Galerkin hierarchy
+ * L^{i+1} = I L^i I^T, a coarsest-level solve, and cascadic refinement
+ * y^j = I^T y^{j+1} followed by Gauss-Seidel sweeps (Alg. 2), power iteration
+ * on the shifted matrix sigma I - L with deflation of the constant vector, and
+ * a final Rayleigh quotient (Sec. 2), stopped by (u^k, u^{k-1}) > 1 - tol
+ * (Sec. 3).  Every step runs in hand-written sm_103a CUDA kernels.
+ *
+ * Conventions shared by every entry point:
+ *  - No exceptions or aborts cross this ABI; every call returns a status.
+ *  - Graphs are symmetric adjacency matrices in CSR form: rowptr[n+1] (int32,
+ *    rowptr[0] = 0, non-decreasing, rowptr[n] = nnz), col[nnz] (int32, strictly
+ *    ascending within a row), w[nnz] (float or double, finite, > 0 off the
+ *    diagonal, w_ij == w_ji bit for bit).  Diagonal entries (self-loops) are
+ *    accepted and dropped.  The Laplacian is L = D - W with d_i = sum_j w_ij.
+ *  - Inputs are borrowed for the duration of the call only.  Device pointers
+ *    must be on the plan's device; host pointers may be pageable or pinned.
+ *  - A plan is not thread-safe: one solve at a time per plan.  Plans on the
+ *    same device may be used from different threads.
+ *  - All device memory the library needs beyond the caller's inputs and
+ *    outputs is owned by the plan (device-side bump arenas, grown on demand
+ *    and kept between solves) and released by fiedler_plan_destroy.
+ */
+#ifndef FIEDLER_H
+#define FIEDLER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FIEDLER_OK = 0,
+  FIEDLER_EAGAIN = 1,            /* fiedler_poll: the ticket is still in flight */
+  FIEDLER_EINVAL = -1,           /* malformed arguments or CSR (see result.bad_index) */
+  FIEDLER_ENOMEM = -2,           /* device memory could not be obtained */
+  FIEDLER_EDISCONNECTED = -3,    /* the graph is not connected: lambda_2 = 0 is degenerate */
+  FIEDLER_ENOTCONVERGED = -4,    /* a power-iteration cap was hit; the result is still returned */
+  FIEDLER_ETIMEOUT = -5,         /* a bounded device-side wait gave up */
+  FIEDLER_ECUDA = -6,            /* a CUDA runtime call failed */
+  FIEDLER_ECANCELED = -7,        /* the ticket was cancelled */
+  FIEDLER_EDEGENERATE = -8,      /* an iterate vanished after deflation (cannot be normalised) */
+  FIEDLER_ENOTSUP = -9           /* a size limit of this build was exceeded */
+} fiedler_status;
+
+/* fiedler_options.precision */
+enum { FIEDLER_FP64 = 0, FIEDLER_FP32_FP64RED = 1 };
+/* fiedler_options.tie_rule: heavy-edge ties broken by a hash of the edge's
+ * vertex indices (then the indices), or by the indices alone */
+enum { FIEDLER_TIE_HASHED = 0, FIEDLER_TIE_INDEX = 1 };
+/* fiedler_graph.w_dtype */
+enum { FIEDLER_W_F32 = 0, FIEDLER_W_F64 = 1 };
+
+typedef struct {
+  int precision;             /* FIEDLER_FP64: values and arithmetic in double.
+                                FIEDLER_FP32_FP64RED: Laplacian values, Gauss-Seidel and the
+                                power-iteration matvec in float; deflation, normalisation,
+                                dot products and the Rayleigh quotient in double. */
+  int coarse_max_n;          /* coarsen while n > coarse_max_n (Alg. 3 uses 25) */
+  int max_levels;            /* at most this many levels, fine level included (<= 32) */
+  double stall_ratio;        /* a coarse level with more than stall_ratio * n vertices is not built */
+  int gs_sweeps;             /* Gauss-Seidel sweeps per level (Alg. 2 with N = gs_sweeps) */
+  int pi_max_iters;          /* power-iteration cap on every level but the coarsest */
+  int pi_max_iters_coarsest; /* power-iteration cap on the coarsest level */
+  double pi_cos_tol;         /* stop when (u^k, u^{k-1}) > 1 - pi_cos_tol (Sec. 3: 1e-6) */
+  double resid_tol;          /* 0: paper stop rule only; > 0: also require ||L u - rho u|| <= resid_tol * sigma */
+  int tie_rule;              /* FIEDLER_TIE_HASHED (default) or FIEDLER_TIE_INDEX */
+  uint64_t seed;             /* random start vector on the coarsest level (splitmix64 stream) */
+  int validate;              /* 1: check the CSR on the device (symmetry, order, weights) */
+  int tail_max_n;            /* levels with n <= tail_max_n run in one thread block; larger
+                                levels run in a cooperative grid-wide kernel */
+  int barrier_timeout_ms;    /* bound on every device-side wait (grid barriers) */
+  int fault_inject;          /* testing only: 1 = one block skips the first grid barrier, so the
+                                others' bounded wait runs out and the solve reports ETIMEOUT */
+} fiedler_options;
+
+typedef struct {
+  int64_t n;                 /* vertices, n >= 2 */
+  int64_t nnz;               /* stored entries, < 2^31 */
+  const int32_t *rowptr;     /* [n + 1] */
+  const int32_t *col;        /* [nnz] */
+  const void *w;             /* [nnz] float or double per w_dtype */
+  int w_dtype;               /* FIEDLER_W_F32 or FIEDLER_W_F64 */
+  int on_device;             /* 1: the three arrays are device pointers; 0: host pointers */
+} fiedler_graph;
+
+typedef struct {
+  double lambda2;            /* Rayleigh quotient x^T L x / x^T x of the returned vector */
+  double residual;           /* ||L x - lambda2 x|| / ||x|| */
+  double ortho;              /* |1^T x| / (sqrt(n) ||x||) */
+  int levels;                /* hierarchy depth, fine level included */
+  int coarsest_n;            /* vertices on the coarsest level */
+  int pi_iters_total;        /* power iterations summed over levels */
+  int gs_sweeps_total;       /* Gauss-Seidel sweeps summed over levels */
+  double *x;                 /* caller-owned output, length n, double; NULL = not wanted.
+                                Unit 2-norm, orthogonal to 1, and sign-normalised so that the
+                                entry of largest |x_i| (lowest index on ties) is positive. */
+  int x_on_device;           /* 1: x is a device pointer; 0: host pointer */
+  float ms;                  /* device time of the solve (CUDA events) */
+  long long bad_index;       /* first offending position when status == FIEDLER_EINVAL, else -1 */
+  fiedler_status status;     /* same value as returned */
+} fiedler_result;
+
+typedef struct fiedler_plan fiedler_plan;
+
+/* Fills opts with the defaults: FP32_FP64RED, coarse_max_n 25, max_levels 30,
+ * stall_ratio 0.9, gs_sweeps 2, pi_max_iters 10000, pi_max_iters_coarsest
+ * 100000, pi_cos_tol 1e-6, resid_tol 0, hashed ties, seed 20160214,
+ * validate 1, tail_max_n 8192, barrier_timeout_ms 5000, fault_inject 0. */
+void fiedler_options_default(fiedler_options *opts);
+
+/* Creates a plan on the current CUDA device.  opts may be NULL (defaults);
+ * cuda_stream is a cudaStream_t on which every solve is ordered, or NULL for a
+ * stream the plan creates.  Errors: EINVAL (bad option), ECUDA, ENOMEM. */
+fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_stream, fiedler_plan **out);
+
+/* Blocking solve of one graph (Alg. 3 + power iteration + Rayleigh quotient).
+ * On return the result fields are filled, and result->x (if non-NULL) holds the
+ * Fiedler vector.  The hierarchy of the last solve stays readable through
+ * fiedler_plan_level_info / fiedler_plan_copy_level until the next solve.
+ * Errors: EINVAL (bad CSR, reported with bad_index), EDISCONNECTED, ENOMEM,
+ * ENOTSUP (nnz >= 2^31, more colours than supported), ETIMEOUT, ECUDA,
+ * EDEGENERATE; ENOTCONVERGED still fills the result. */
+fiedler_status fiedler_solve(fiedler_plan *plan, const fiedler_graph *graph, fiedler_result *result);
+
+/* Asynchronous form: copies the graph (host or device) into plan-owned memory,
+ * queues the solve and returns a ticket at once.  Thread-safe against
+ * fiedler_poll and fiedler_cancel on the same plan. */
+fiedler_status fiedler_batch_submit(fiedler_plan *plan, const fiedler_graph *graph, uint64_t *ticket);
+
+/* Waits up to timeout_ms (0 = do not wait, < 0 = wait forever) for a ticket.
+ * Returns EAGAIN while it is in flight; otherwise the solve's status with
+ * result filled as by fiedler_solve (result->x must have room for n doubles,
+ * host or device per x_on_device).  A finished ticket is forgotten after a
+ * successful poll. */
+fiedler_status fiedler_poll(fiedler_plan *plan, uint64_t ticket, int timeout_ms, fiedler_result *result);
+
+/* Cancels a queued ticket (ECANCELED on its next poll); a ticket already on
+ * the GPU completes normally.  EINVAL for unknown tickets. */
+fiedler_status fiedler_cancel(fiedler_plan *plan, uint64_t ticket);
+
+/* Releases the plan, its stream (if owned) and all its device memory. */
+void fiedler_plan_destroy(fiedler_plan *plan);
+
+/* Static English description of a status. */
+const char *fiedler_status_str(fiedler_status status);
+
+/* ---- introspection of the last solve (tests, profiling) ---------------- */
+
+typedef struct {
+  int64_t n, nnz;            /* level size (setup operator, self-loops dropped) */
+  int nc;                    /* vertices of the next level (0 on the coarsest) */
+  int ncolors;               /* colour classes used by the multicolour Gauss-Seidel */
+  int match_rounds;          /* handshake rounds of the heavy-edge matching */
+  int color_rounds;          /* Jones-Plassmann rounds */
+  int gs_sweeps;             /* Gauss-Seidel sweeps kept on this level */
+  int pi_iters;              /* power iterations on this level */
+  double sigma;              /* shift: 2 max_i d_i */
+  double last_cos;           /* (u^k, u^{k-1}) of the last power iteration */
+} fiedler_level_info;
+
+/* Number of levels of the last solve (0 before any solve). */
+int fiedler_plan_num_levels(const fiedler_plan *plan);
+
+/* Sizes and counters of level l of the last solve.  EINVAL if l is out of range. */
+fiedler_status fiedler_plan_level_info(const fiedler_plan *plan, int level, fiedler_level_info *info);
+
+/* Copies level l of the last solve to HOST arrays in the graph's own vertex
+ * numbering (any pointer may be NULL): the Laplacian's off-diagonal part as
+ * CSR (rowptr[n+1], col[nnz], w[nnz] as double), its diagonal d[n], the
+ * aggregate map agg[n] to level l+1 (left untouched on the coarsest level),
+ * the matching mate[n] (-1 = unmatched) and the colour of every vertex. */
+fiedler_status fiedler_plan_copy_level(const fiedler_plan *plan, int level, int32_t *rowptr, int32_t *col,
+                                       double *w, double *d, int32_t *agg, int32_t *mate, int32_t *color);
+
+typedef struct {
+  uint64_t kernel_launches;  /* kernels launched by the last solve */
+  int n_kernels;             /* entries used in the arrays below */
+  const char *kernel_name[4];
+  int kernel_launches_by[4]; /* launches of each kernel in the last solve */
+  float kernel_ms[4];        /* CUDA-event time of each kernel in the last solve (profiling on) */
+  double kernel_bytes[4];    /* algorithmic bytes moved by each kernel in the last solve */
+  int n_phases;
+  const char *phase_name[16];
+  double phase_ms[2][16];    /* device-timer time per phase, [0] grid-wide kernel, [1] one-block kernel */
+  double phase_bytes[2][16]; /* algorithmic bytes per phase, same split */
+} fiedler_profile;
+
+/* 1: record CUDA events around every kernel of the following solves. */
+fiedler_status fiedler_plan_set_profiling(fiedler_plan *plan, int on);
+
+/* Counters of the last solve. */
+fiedler_status fiedler_plan_get_profile(const fiedler_plan *plan, fiedler_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIEDLER_H */

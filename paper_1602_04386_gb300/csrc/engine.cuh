@@ -1,0 +1,1503 @@
+// engine.cuh -- the level engine of the cascadic multigrid Fiedler solver.
+//
+// One templated engine walks the whole method of Alg. 3 on the device:
+//   setup   (Alg. 1 + Alg. 3 step 1): ingest (Def 2.1), colouring + colour-order
+//           copy of each level, heavy-edge matching, aggregation, Galerkin
+//           coarse operator L^{i+1} = I L^i I^T, until n <= coarse_max_n;
+//   coarsest (Alg. 3 step 2): connectivity check, random start, Gauss-Seidel
+//           sweeps (Alg. 2) and power iteration on sigma I - L;
+//   refinement (Alg. 3 step 3): y^j = I^T y^{j+1}, Gauss-Seidel sweeps, power
+//           iteration with deflation of the constant vector;
+//   final:  Rayleigh quotient, residual, orthogonality, sign (Sec. 2).
+//
+// The same code runs in two shapes.  GRID = true: a cooperative launch over
+// all SMs, phases separated by a bounded grid barrier, for levels with
+// n > tail_max_n.  GRID = false: one 1024-thread block with __syncthreads, for
+// the small levels at the bottom of the hierarchy, where grid barriers would
+// dominate.  Every thread of every block runs the same control flow: decisions
+// are taken from grid reductions that every block finishes redundantly (same
+// data, same order, same result), and arena offsets are advanced identically
+// by every thread, so no extra barrier is needed to publish them.
+#pragma once
+#include <cuda_runtime.h>
+#include <float.h>
+#include <limits.h>
+#include <stdint.h>
+
+#include "fz_state.h"
+
+namespace fz {
+
+#define FZD __device__ __forceinline__
+
+// ---------------------------------------------------------------------------
+// splitmix64 (S. Vigna): output k of the stream seeded with s is
+// mix(s + (k + 1) * 0x9E3779B97F4A7C15).  Used for the heavy-edge tie-break
+// hash, the colouring priority and the coarsest-level random start.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+FZD uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+FZD uint64_t sm64(uint64_t seed, uint64_t k) { return mix64(seed + (k + 1) * kGamma); }
+FZD uint64_t edge_hash(int lo, int hi) { return sm64(((uint64_t)(uint32_t)lo << 32) | (uint32_t)hi, 0); }
+FZD uint64_t vtx_hash(int v) { return sm64((uint64_t)(uint32_t)v, 0); }
+FZD double uniform01(uint64_t seed, uint64_t k) {
+  return (double)(sm64(seed, k) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+FZD uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Heavy-edge order K(e) = (w desc, h(min,max) asc, min asc, max asc); the hash
+// is only evaluated when weights tie exactly.
+struct Best {
+  double w;
+  int v, lo, hi;
+  uint64_t h;
+  int hok;
+};
+FZD void best_init(Best &b) {
+  b.v = -1;
+  b.hok = 0;
+}
+FZD bool best_beats(Best &b, double w, int u, int v, int tie) {
+  if (b.v < 0) return true;
+  if (w != b.w) return w > b.w;
+  int lo = min(u, v), hi = max(u, v);
+  if (tie == 0) {
+    if (!b.hok) {
+      b.h = edge_hash(b.lo, b.hi);
+      b.hok = 1;
+    }
+    uint64_t h = edge_hash(lo, hi);
+    if (h != b.h) return h < b.h;
+  }
+  if (lo != b.lo) return lo < b.lo;
+  return hi < b.hi;
+}
+FZD void best_set(Best &b, double w, int u, int v) {
+  b.w = w;
+  b.v = v;
+  b.lo = min(u, v);
+  b.hi = max(u, v);
+  b.hok = 0;
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+FZD void red_init(Red &r) {
+#pragma unroll
+  for (int k = 0; k < 6; k++) r.s[k] = 0.0;
+  r.mx = -DBL_MAX;
+  r.mxi = INT_MAX;
+  r.cnt = 0;
+}
+FZD void red_add(Red &a, const Red &b) {
+#pragma unroll
+  for (int k = 0; k < 6; k++) a.s[k] += b.s[k];
+  if (b.mx > a.mx || (b.mx == a.mx && b.mxi < a.mxi)) {
+    a.mx = b.mx;
+    a.mxi = b.mxi;
+  }
+  a.cnt += b.cnt;
+}
+FZD void red_shfl(Red &r, int off) {
+  Red o;
+#pragma unroll
+  for (int k = 0; k < 6; k++) o.s[k] = __shfl_xor_sync(0xffffffffu, r.s[k], off);
+  o.mx = __shfl_xor_sync(0xffffffffu, r.mx, off);
+  o.mxi = __shfl_xor_sync(0xffffffffu, r.mxi, off);
+  o.cnt = __shfl_xor_sync(0xffffffffu, r.cnt, off);
+  red_add(r, o);
+}
+FZD void warp_red(Red &r) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) red_shfl(r, off);
+}
+
+// exclusive block scan of an int; *total = block sum.  All threads must call.
+FZD int block_scan(int v, int *total) {
+  __shared__ int ws[33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = lane < nw ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    ws[lane] = t;
+  }
+  __syncthreads();
+  int incl = x + (w > 0 ? ws[w - 1] : 0);
+  *total = ws[nw - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+// ---------------------------------------------------------------------------
+// sorting of short segments: one thread (insertion) or one block (bitonic
+// network for any length: merge blocks start with a reversed-partner step, so
+// missing elements past len act as +infinity and are never touched)
+template <class K>
+FZD void thread_sort(K *a, int len) {
+  for (int i = 1; i < len; i++) {
+    K v = a[i];
+    int j = i - 1;
+    while (j >= 0 && a[j] > v) {
+      a[j + 1] = a[j];
+      j--;
+    }
+    a[j + 1] = v;
+  }
+}
+
+template <class K>
+FZD void block_bitonic(K *a, int len) {
+  int P = 1;
+  while (P < len) P <<= 1;
+  for (int k = 2; k <= P; k <<= 1) {
+    const int half = k >> 1;
+    for (int p = threadIdx.x; p < (P >> 1); p += blockDim.x) {
+      int blk = p / half, t = p - blk * half;
+      int i = blk * k + t, j = blk * k + k - 1 - t;
+      if (j < len) {
+        K x = a[i], y = a[j];
+        if (y < x) {
+          a[i] = y;
+          a[j] = x;
+        }
+      }
+    }
+    __syncthreads();
+    for (int jj = k >> 2; jj >= 1; jj >>= 1) {
+      for (int p = threadIdx.x; p < (P >> 1); p += blockDim.x) {
+        int blk = p / jj, t = p - blk * jj;
+        int i = blk * 2 * jj + t, j = i + jj;
+        if (j < len) {
+          K x = a[i], y = a[j];
+          if (y < x) {
+            a[i] = y;
+            a[j] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+constexpr int kShSort = 2048;  // shared staging for block sorts (u64 keys)
+constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one thread
+
+// static __shared__ storage declared in a function is one allocation per kernel
+FZD uint64_t *sh_raw() {
+  __shared__ uint64_t raw[kShSort];
+  return raw;
+}
+FZD int *sh_list() {
+  __shared__ int list[kCtaThreads];
+  return list;
+}
+FZD int *sh_ints() {
+  __shared__ int v[8];
+  return v;
+}
+
+template <class K>
+FZD void block_sort(K *g, int len) {
+  K *s = reinterpret_cast<K *>(sh_raw());
+  const int cap = (int)(kShSort * sizeof(uint64_t) / sizeof(K));
+  if (len <= cap) {
+    for (int i = threadIdx.x; i < len; i += blockDim.x) s[i] = g[i];
+    __syncthreads();
+    block_bitonic(s, len);
+    for (int i = threadIdx.x; i < len; i += blockDim.x) g[i] = s[i];
+    __syncthreads();
+  } else {
+    block_bitonic(g, len);
+  }
+}
+
+// ---------------------------------------------------------------------------
+struct GalerkinScratch {
+  int *cnt, *fill, *tcnt, *aggptr, *segptr, *members, *cc, *memoff, *dcnt;
+  uint64_t *keys;
+  double *segw;
+};
+
+template <class T, bool GRID>
+struct Eng {
+  State *S;
+  int tid, nthr, bid, nb, rb, kind;
+  unsigned long long aoff, soff;
+  // control flow, identical in every thread
+  int nlevels, setup_done, coarsest, coarsest_solved, solved, finalized;
+
+  // ---- infrastructure ------------------------------------------------------
+  FZD void init(State *s) {
+    S = s;
+    bid = blockIdx.x;
+    nb = gridDim.x;
+    tid = blockIdx.x * blockDim.x + threadIdx.x;
+    nthr = gridDim.x * blockDim.x;
+    rb = 0;
+    kind = GRID ? 0 : 1;
+    aoff = S->arena_off;
+    soff = 0;
+    nlevels = S->nlevels;
+    setup_done = S->setup_done;
+    coarsest = S->coarsest;
+    coarsest_solved = S->coarsest_solved;
+    solved = S->solved;
+    finalized = S->finalized;
+    if (bid == 0 && threadIdx.x == 0) S->t_last = gtime();
+  }
+  FZD bool lead() const { return bid == 0 && threadIdx.x == 0; }
+  FZD void fail(int code) { atomicCAS(&S->status, 0, code); }
+  FZD int status() const { return *(volatile int *)&S->status; }
+  FZD void persist() {
+    if (lead()) {
+      S->nlevels = nlevels;
+      S->setup_done = setup_done;
+      S->coarsest = coarsest;
+      S->coarsest_solved = coarsest_solved;
+      S->solved = solved;
+      S->finalized = finalized;
+      if (status() == 0) S->arena_off = aoff;
+    }
+  }
+
+  FZD void *aalloc(unsigned long long bytes) {
+    unsigned long long sz = (bytes + 255ull) & ~255ull;
+    if (aoff + sz > S->arena_size) {
+      fail(ST_ARENA);
+      return nullptr;
+    }
+    void *p = S->arena + aoff;
+    aoff += sz;
+    return p;
+  }
+  FZD void *salloc(unsigned long long bytes) {
+    unsigned long long sz = (bytes + 255ull) & ~255ull;
+    if (soff + sz > S->scratch_size) {
+      fail(ST_SCRATCH);
+      return nullptr;
+    }
+    void *p = S->scratch + soff;
+    soff += sz;
+    return p;
+  }
+
+  // barrier over every participating thread; false if the solve has failed
+  FZD bool sync() {
+    if (!GRID) return __syncthreads_and(status() == 0);
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      volatile unsigned *genp = &S->bar_gen;
+      unsigned g = *genp;
+      __threadfence();
+      unsigned arrived = atomicAdd(&S->bar_count, 1u);
+      if (arrived == (unsigned)nb - 1u) {
+        // every block has arrived, so every failure of the phase is visible:
+        // snapshot the verdict for all blocks before releasing them
+        atomicExch(&S->bar_count, 0u);
+        *(volatile int *)&S->bar_ok = status() == 0;
+        __threadfence();
+        atomicAdd(&S->bar_gen, 1u);
+      } else {
+        const uint64_t t0 = gtime();
+        const uint64_t lim = S->opt.barrier_timeout_ns;
+        unsigned spins = 0;
+        while (*genp == g) {
+          if ((++spins & 255u) == 0u && gtime() - t0 > lim) {
+            fail(ST_ETIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+      s_ok = (*genp != g) ? *(volatile int *)&S->bar_ok : 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  }
+
+  // profile: attribute the time since the last mark to phase ph
+  FZD void mark(int ph, double bytes) {
+    if (lead()) {
+      uint64_t t = gtime();
+      S->phase_ns[kind][ph] += (double)(t - S->t_last);
+      S->phase_bytes[kind][ph] += bytes;
+      S->t_last = t;
+    }
+  }
+
+  FZD void chunk(long long n, int &lo, int &hi) const {
+    long long ch = (n + nb - 1) / nb;
+    long long a = (long long)bid * ch;
+    if (a > n) a = n;
+    long long b = a + ch;
+    if (b > n) b = n;
+    lo = (int)a;
+    hi = (int)b;
+  }
+
+  // Grid-wide reduction of per-thread partials.  On return r holds the total
+  // in every thread; *pre_cnt / *pre_s0 receive the sums of cnt / s[0] over
+  // the blocks before this one (for chunked scans).
+  FZD bool grid_reduce(Red &r, long long *pre_cnt = nullptr, double *pre_s0 = nullptr) {
+    __shared__ Red s_w[32];
+    __shared__ Red s_tot;
+    __shared__ long long s_pc;
+    __shared__ double s_ps;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_red(r);
+    if (lane == 0) s_w[w] = r;
+    __syncthreads();
+    Red *part = S->part + rb * kMaxBlocks;
+    if (w == 0) {
+      Red a;
+      red_init(a);
+      if (lane < nw) a = s_w[lane];
+      warp_red(a);
+      if (lane == 0) {
+        if (GRID) part[bid] = a;
+        else s_tot = a;
+      }
+    }
+    if (GRID) {
+      if (!sync()) return false;
+      if (w == 0) {
+        Red a;
+        red_init(a);
+        long long pc = 0;
+        double ps = 0.0;
+        for (int b = lane; b < nb; b += 32) {
+          Red p = part[b];
+          if (b < bid) {
+            pc += p.cnt;
+            ps += p.s[0];
+          }
+          red_add(a, p);
+        }
+        warp_red(a);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+          pc += __shfl_xor_sync(0xffffffffu, pc, off);
+          ps += __shfl_xor_sync(0xffffffffu, ps, off);
+        }
+        if (lane == 0) {
+          s_tot = a;
+          s_pc = pc;
+          s_ps = ps;
+        }
+      }
+    } else {
+      if (threadIdx.x == 0) {
+        s_pc = 0;
+        s_ps = 0.0;
+      }
+      if (!__syncthreads_and(status() == 0)) return false;
+    }
+    __syncthreads();
+    r = s_tot;
+    if (pre_cnt) *pre_cnt = s_pc;
+    if (pre_s0) *pre_s0 = s_ps;
+    __syncthreads();
+    rb ^= 1;
+    return true;
+  }
+
+  // setup weights: FP64 on coarse levels, the caller's float or double on the fine level
+  struct W {
+    const double *w64;
+    const float *w32;
+    FZD double operator[](int e) const { return w64 ? w64[e] : (double)w32[e]; }
+  };
+  FZD static W wof(const Level *L) { return W{L->w64, L->w32}; }
+
+  FZD bool elig(int n) const { return GRID ? (n > S->opt.tail_max_n) : (n <= S->opt.tail_max_n); }
+
+  // ---- A1: ingest the fine level (Def 2.1) ---------------------------------
+  FZD bool ingest() {
+    const int n = S->n0, nnz = S->nnz0;
+    const int *rp = S->in_rowptr, *ci = S->in_col;
+    const bool wf64 = S->in_w_f64 != 0;
+    const double *wd = (const double *)S->in_w;
+    const float *wf = (const float *)S->in_w;
+    const int validate = S->opt.validate;
+    if (validate) {
+      for (int i = tid; i <= n; i += nthr) {
+        int a = rp[i];
+        bool bad = a < 0 || a > nnz || (i == 0 && a != 0) || (i == n && a != nnz) || (i < n && rp[i + 1] < a);
+        if (bad) {
+          atomicMin((unsigned long long *)&S->bad_index, (unsigned long long)i);
+          fail(ST_EINVAL);
+        }
+      }
+      if (!sync()) return false;
+    }
+    double *d = (double *)aalloc(8ull * n);
+    if (!d) return false;
+    int lo, hi;
+    chunk(n, lo, hi);
+    Red r;
+    red_init(r);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const int e0 = rp[i], e1 = rp[i + 1];
+      double di = 0.0;
+      int loops = 0;
+      for (int e = e0; e < e1; e++) {
+        const int j = ci[e];
+        const double w = wf64 ? wd[e] : (double)wf[e];
+        if (validate) {
+          bool bad = j < 0 || j >= n || (e > e0 && ci[e - 1] >= j) || !isfinite(w) || (j != i && !(w > 0.0));
+          if (!bad && j != i) {
+            int a = rp[j], b = rp[j + 1] - 1, f = -1;
+            while (a <= b) {
+              int m = (a + b) >> 1, cm = ci[m];
+              if (cm == i) {
+                f = m;
+                break;
+              }
+              if (cm < i) a = m + 1;
+              else b = m - 1;
+            }
+            bad = f < 0 || (wf64 ? wd[f] : (double)wf[f]) != w;
+          }
+          if (bad) {
+            atomicMin((unsigned long long *)&S->bad_index, (unsigned long long)e);
+            fail(ST_EINVAL);
+            break;
+          }
+        }
+        if (j == i) {
+          loops++;
+          continue;
+        }
+        di += w;
+      }
+      d[i] = di;
+      r.cnt += e1 - e0 - loops;
+      r.s[0] += (double)loops;
+      r.mx = fmax(r.mx, di);
+    }
+    long long pre = 0;
+    if (!grid_reduce(r, &pre)) return false;
+    const long long m = r.cnt;
+    const double maxd = r.mx;
+    int *rowptr = (int *)rp, *col = (int *)ci;
+    double *w64 = wf64 ? (double *)wd : nullptr;
+    float *w32 = wf64 ? nullptr : (float *)wf;
+    if (r.s[0] > 0.0) {  // drop self-loops
+      rowptr = (int *)aalloc(4ull * (n + 1));
+      col = (int *)aalloc(4ull * (m > 0 ? m : 1));
+      void *wn = aalloc((wf64 ? 8ull : 4ull) * (m > 0 ? m : 1));
+      if (!rowptr || !col || !wn) return false;
+      w64 = wf64 ? (double *)wn : nullptr;
+      w32 = wf64 ? nullptr : (float *)wn;
+      long long run = pre;
+      for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+        int i = t0 + threadIdx.x;
+        int kept = 0;
+        if (i < hi)
+          for (int e = rp[i]; e < rp[i + 1]; e++) kept += ci[e] != i;
+        int tot;
+        int ex = block_scan(kept, &tot);
+        if (i < hi) {
+          int o = (int)(run + ex);
+          rowptr[i] = o;
+          for (int e = rp[i]; e < rp[i + 1]; e++) {
+            if (ci[e] == i) continue;
+            col[o] = ci[e];
+            if (wf64) w64[o] = wd[e];
+            else w32[o] = wf[e];
+            o++;
+          }
+        }
+        run += tot;
+      }
+      if (hi == n && lo < hi) rowptr[n] = (int)m;
+      if (n > 0 && lo == hi && bid == nb - 1) rowptr[n] = (int)m;
+    }
+    if (lead()) {
+      Level &L = S->lv[0];
+      L.n = n;
+      L.nnz = (int)m;
+      L.rowptr = rowptr;
+      L.col = col;
+      L.w64 = w64;
+      L.w32 = w32;
+      L.d = d;
+      L.sigma = 2.0 * maxd;
+    }
+    if (!sync()) return false;
+    mark(PH_INGEST, 12.0 * n + (4.0 + (wf64 ? 8.0 : 4.0)) * nnz * (validate ? 2.0 : 1.0));
+    return true;
+  }
+
+  // ---- A6: Jones-Plassmann colouring, priority (h(v), v) --------------------
+  FZD bool colour(int l) {
+    Level *L = &S->lv[l];
+    const int n = L->n;
+    const int *rp = L->rowptr, *ci = L->col;
+    soff = 0;
+    int *cround = (int *)salloc(4ull * n);
+    int *color = (int *)aalloc(4ull * n);
+    if (!cround || !color) return false;
+    for (int v = tid; v < n; v += nthr) cround[v] = INT_MAX;
+    if (!sync()) return false;
+    int maxc = -1, r = 0;
+    for (;; r++) {
+      Red red;
+      red_init(red);
+      for (int v = tid; v < n; v += nthr) {
+        if (cround[v] != INT_MAX) continue;
+        const uint64_t hv = vtx_hash(v);
+        bool top = true;
+        const int e0 = rp[v], e1 = rp[v + 1];
+        for (int e = e0; e < e1; e++) {
+          const int u = ci[e];
+          if (cround[u] >= r) {
+            const uint64_t hu = vtx_hash(u);
+            if (hu > hv || (hu == hv && u > v)) {
+              top = false;
+              break;
+            }
+          }
+        }
+        if (!top) {
+          red.cnt++;
+          continue;
+        }
+        int base = 0, c = 0;
+        for (;;) {
+          uint64_t m = 0;
+          for (int e = e0; e < e1; e++) {
+            const int u = ci[e];
+            if (cround[u] < r) {
+              const int cu = color[u] - base;
+              if (cu >= 0 && cu < 64) m |= 1ull << cu;
+            }
+          }
+          if (m != ~0ull) {
+            c = base + __ffsll((long long)~m) - 1;
+            break;
+          }
+          base += 64;
+        }
+        color[v] = c;
+        cround[v] = r;
+        red.mx = fmax(red.mx, (double)c);
+      }
+      if (!grid_reduce(red)) return false;
+      if (red.mx >= 0.0) maxc = max(maxc, (int)red.mx);
+      if (red.cnt == 0) break;
+    }
+    const int ncol = maxc + 1;
+    if (ncol > kMaxColors) {
+      fail(ST_ENOTSUP);
+      return false;
+    }
+    if (lead()) {
+      L->color = color;
+      L->ncolors = ncol;
+      L->color_rounds = r + 1;
+    }
+    if (!sync()) return false;
+    mark(PH_COLOR, (double)(r + 1) * (8.0 * n + 8.0 * L->nnz));
+    return true;
+  }
+
+  // ---- colour-order copy of the level for the solve phase -------------------
+  FZD bool reorder(int l) {
+    Level *L = &S->lv[l];
+    const int n = L->n, nnz = L->nnz, C = L->ncolors;
+    const int *rp = L->rowptr, *ci = L->col, *color = L->color;
+    int *hist = (int *)salloc(4ull * C * nb);
+    int *perm = (int *)aalloc(4ull * n);
+    int *iperm = (int *)aalloc(4ull * n);
+    int *colstart = (int *)aalloc(4ull * (C + 1));
+    int *srp = (int *)aalloc(4ull * (n + 1));
+    int *scol = (int *)aalloc(4ull * (nnz > 0 ? nnz : 1));
+    T *sw = (T *)aalloc(sizeof(T) * (unsigned long long)(nnz > 0 ? nnz : 1));
+    T *x = (T *)aalloc(sizeof(T) * (unsigned long long)n);
+    T *y = (T *)aalloc(sizeof(T) * (unsigned long long)n);
+    int *sagg = (int *)aalloc(4ull * n);
+    if (!hist || !perm || !iperm || !colstart || !srp || !scol || !sw || !x || !y || !sagg) return false;
+    int *sh_cnt = reinterpret_cast<int *>(sh_raw());  // [kMaxColors]
+    int *sh_base = sh_cnt + kMaxColors;              // [kMaxColors]
+    int(*wc)[64] = reinterpret_cast<int(*)[64]>(sh_base + kMaxColors);  // [32][64], C <= 64 only
+    int lo, hi;
+    chunk(n, lo, hi);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) sh_cnt[c] = 0;
+    __syncthreads();
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) atomicAdd(&sh_cnt[color[v]], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) hist[(size_t)c * nb + bid] = sh_cnt[c];
+    if (!sync()) return false;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+      int t = 0, p = 0;
+      for (int b = 0; b < nb; b++) {
+        int h = hist[(size_t)c * nb + b];
+        t += h;
+        if (b < bid) p += h;
+      }
+      sh_cnt[c] = t;
+      sh_base[c] = p;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int c = 0; c < C; c++) {
+        if (bid == 0) colstart[c] = acc;
+        sh_base[c] += acc;
+        acc += sh_cnt[c];
+      }
+      if (bid == 0) colstart[C] = acc;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (C <= 64) {
+      for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+        const int v = t0 + threadIdx.x;
+        const int cv = v < hi ? color[v] : -1;
+        for (int k = threadIdx.x; k < nw * 64; k += blockDim.x) wc[k >> 6][k & 63] = 0;
+        __syncthreads();
+        const unsigned peers = __match_any_sync(0xffffffffu, cv);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (cv >= 0 && rank == 0) wc[w][cv] = __popc(peers);
+        __syncthreads();
+        if (threadIdx.x < C) {
+          const int c = threadIdx.x;
+          int acc = sh_base[c];
+          for (int ww = 0; ww < nw; ww++) {
+            int t = wc[ww][c];
+            wc[ww][c] = acc;
+            acc += t;
+          }
+          sh_base[c] = acc;
+        }
+        __syncthreads();
+        if (cv >= 0) {
+          const int pos = wc[w][cv] + rank;
+          perm[pos] = v;
+          iperm[v] = pos;
+        }
+        __syncthreads();
+      }
+    } else {
+      for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+        const int v = t0 + threadIdx.x;
+        const int cv = v < hi ? color[v] : -1;
+        for (int c = 0; c < C; c++) {
+          if (!__syncthreads_or(cv == c)) continue;
+          int tot;
+          int ex = block_scan(cv == c, &tot);
+          if (cv == c) {
+            const int pos = sh_base[c] + ex;
+            perm[pos] = v;
+            iperm[v] = pos;
+          }
+          __syncthreads();
+          if (threadIdx.x == 0) sh_base[c] += tot;
+          __syncthreads();
+        }
+      }
+    }
+    if (!sync()) return false;
+    // row pointers of the colour-order copy
+    Red red;
+    red_init(red);
+    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+      const int v = perm[k];
+      red.cnt += rp[v + 1] - rp[v];
+    }
+    long long pre = 0;
+    if (!grid_reduce(red, &pre)) return false;
+    long long run = pre;
+    const W wl = wof(L);
+    for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+      const int k = t0 + threadIdx.x;
+      const int v = k < hi ? perm[k] : 0;
+      const int deg = k < hi ? rp[v + 1] - rp[v] : 0;
+      int tot;
+      const int ex = block_scan(deg, &tot);
+      if (k < hi) {
+        int o = (int)(run + ex);
+        srp[k] = o;
+        for (int e = rp[v]; e < rp[v + 1]; e++, o++) {
+          scol[o] = iperm[ci[e]];
+          sw[o] = (T)wl[e];
+        }
+      }
+      run += tot;
+    }
+    if (lead()) srp[n] = nnz;
+    // solve positions of the previous level map through this level's order
+    if (l > 0) {
+      Level *F = &S->lv[l - 1];
+      const int nf = F->n;
+      const int *fperm = F->perm, *fagg = F->agg;
+      int *fsagg = F->sagg;
+      for (int k = tid; k < nf; k += nthr) fsagg[k] = iperm[fagg[fperm[k]]];
+    }
+    if (lead()) {
+      L->perm = perm;
+      L->iperm = iperm;
+      L->colstart = colstart;
+      L->srowptr = srp;
+      L->scol = scol;
+      L->sw = sw;
+      L->x = x;
+      L->y = y;
+      L->sagg = sagg;
+    }
+    if (!sync()) return false;
+    mark(PH_REORDER, 28.0 * n + (8.0 + (L->w64 ? 8.0 : 4.0) + 4.0 + sizeof(T)) * nnz);
+    return true;
+  }
+
+  // ---- A2: heavy-edge matching by handshake rounds ---------------------------
+  FZD bool match(int l) {
+    Level *L = &S->lv[l];
+    const int n = L->n;
+    const int *rp = L->rowptr, *ci = L->col;
+    const int tie = S->opt.tie_rule;
+    const W wl = wof(L);
+    int *mate = (int *)aalloc(4ull * n);
+    int *cand = (int *)salloc(4ull * n);
+    if (!mate || !cand) return false;
+    int r = 0;
+    double bytes = 0.0;
+    for (;; r++) {
+      Red red;
+      red_init(red);
+      for (int v = tid; v < n; v += nthr) {
+        if (r == 0) mate[v] = -1;
+        else if (mate[v] >= 0 || cand[v] == -2) continue;
+        Best b;
+        best_init(b);
+        for (int e = rp[v]; e < rp[v + 1]; e++) {
+          const int u = ci[e];
+          if (r > 0 && mate[u] >= 0) continue;
+          const double wv = wl[e];
+          if (best_beats(b, wv, v, u, tie)) best_set(b, wv, v, u);
+        }
+        cand[v] = b.v >= 0 ? b.v : -2;
+        red.cnt += b.v >= 0;
+        red.s[0] += (double)(rp[v + 1] - rp[v]);
+      }
+      if (!grid_reduce(red)) return false;
+      bytes += 12.0 * n + red.s[0] * (8.0 + (L->w64 ? 8.0 : 4.0));
+      if (red.cnt == 0) break;
+      for (int v = tid; v < n; v += nthr) {
+        const int c = cand[v];
+        if (c >= 0 && cand[c] == v) mate[v] = c;
+      }
+      if (!sync()) return false;
+    }
+    if (lead()) {
+      L->mate = mate;
+      L->match_rounds = r;
+    }
+    if (!sync()) return false;
+    mark(PH_MATCH, bytes);
+    return true;
+  }
+
+  // ---- A3: aggregates from the matching; returns nc (or -1: stop coarsening)
+  FZD bool aggregate(int l, int &nc_out, GalerkinScratch &G) {
+    Level *L = &S->lv[l];
+    const int n = L->n;
+    const int *rp = L->rowptr, *ci = L->col, *mate = L->mate;
+    const int tie = S->opt.tie_rule;
+    const W wl = wof(L);
+    const double stall = S->opt.stall_ratio;
+    int lo, hi;
+    chunk(n, lo, hi);
+    Red red;
+    red_init(red);
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+      const int m = mate[v];
+      red.cnt += (m >= 0) ? (v < m) : (rp[v + 1] == rp[v]);
+    }
+    long long pre = 0;
+    if (!grid_reduce(red, &pre)) return false;
+    const long long nc = red.cnt;
+    nc_out = -1;
+    if (nc < 2 || (double)nc > stall * (double)n) return true;
+    int *agg = (int *)aalloc(4ull * n);
+    G.cnt = (int *)salloc(4ull * nc);
+    G.fill = (int *)salloc(4ull * nc);
+    G.tcnt = (int *)salloc(4ull * nc);
+    G.aggptr = (int *)salloc(4ull * (nc + 1));
+    G.segptr = (int *)salloc(4ull * (nc + 1));
+    G.dcnt = (int *)salloc(4ull * nc);
+    G.members = (int *)salloc(4ull * n);
+    G.cc = (int *)salloc(4ull * n);
+    G.memoff = (int *)salloc(4ull * n);
+    if (!agg || !G.cnt || !G.fill || !G.tcnt || !G.aggptr || !G.segptr || !G.dcnt || !G.members || !G.cc ||
+        !G.memoff)
+      return false;
+    long long run = pre;
+    for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+      const int v = t0 + threadIdx.x;
+      int f = 0;
+      if (v < hi) {
+        const int m = mate[v];
+        f = (m >= 0) ? (v < m) : (rp[v + 1] == rp[v]);
+      }
+      int tot;
+      const int ex = block_scan(f, &tot);
+      if (f) agg[v] = (int)(run + ex);
+      run += tot;
+    }
+    for (long long I = tid; I < nc; I += nthr) {
+      G.cnt[I] = 0;
+      G.fill[I] = 0;
+      G.tcnt[I] = 0;
+    }
+    if (!sync()) return false;
+    for (int v = tid; v < n; v += nthr) {
+      const int m = mate[v];
+      int a;
+      if (m >= 0) {
+        a = agg[v < m ? v : m];
+        if (v > m) agg[v] = a;
+      } else if (rp[v + 1] == rp[v]) {
+        a = agg[v];
+      } else {
+        Best b;
+        best_init(b);
+        for (int e = rp[v]; e < rp[v + 1]; e++) {
+          const int u = ci[e];
+          const double wv = wl[e];
+          if (best_beats(b, wv, v, u, tie)) best_set(b, wv, v, u);
+        }
+        const int u = b.v, mu = mate[u];
+        if (mu < 0) {  // matching not maximal: cannot happen
+          fail(ST_EINVAL);
+          a = 0;
+        } else {
+          a = agg[u < mu ? u : mu];
+        }
+        agg[v] = a;
+      }
+      atomicAdd(&G.cnt[a], 1);
+    }
+    if (lead()) {  // published before the barrier: the Galerkin phase reads it
+      L->agg = agg;
+      L->nc = (int)nc;
+    }
+    if (!sync()) return false;
+    mark(PH_AGG, 24.0 * n + 12.0 * L->nnz);
+    nc_out = (int)nc;
+    return true;
+  }
+
+  // ---- A4: Galerkin coarse operator I L I^T ---------------------------------
+  FZD bool galerkin(int l, int nc, GalerkinScratch &G) {
+    Level *L = &S->lv[l];
+    const int n = L->n;
+    const int *rp = L->rowptr, *ci = L->col;
+    const int *agg = L->agg;
+    const W wl = wof(L);
+    // G1: cross-aggregate entries per fine row and per aggregate
+    for (int v = tid; v < n; v += nthr) {
+      const int I = agg[v];
+      int k = 0;
+      for (int e = rp[v]; e < rp[v + 1]; e++) k += agg[ci[e]] != I;
+      G.cc[v] = k;
+      if (k) atomicAdd(&G.tcnt[I], k);
+    }
+    if (!sync()) return false;
+    // G2: member and segment pointers (chunked scans over aggregates)
+    int lo, hi;
+    chunk(nc, lo, hi);
+    Red red;
+    red_init(red);
+    for (int I = lo + threadIdx.x; I < hi; I += blockDim.x) {
+      red.cnt += G.cnt[I];
+      red.s[0] += (double)G.tcnt[I];
+    }
+    long long preA = 0;
+    double preB = 0.0;
+    if (!grid_reduce(red, &preA, &preB)) return false;
+    const long long ttot = (long long)red.s[0];
+    {
+      long long ra = preA, rbb = (long long)preB;
+      for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+        const int I = t0 + threadIdx.x;
+        const int a = I < hi ? G.cnt[I] : 0, b = I < hi ? G.tcnt[I] : 0;
+        int ta, tb;
+        const int ea = block_scan(a, &ta);
+        const int eb = block_scan(b, &tb);
+        if (I < hi) {
+          G.aggptr[I] = (int)(ra + ea);
+          G.segptr[I] = (int)(rbb + eb);
+        }
+        ra += ta;
+        rbb += tb;
+      }
+      if (lead()) {
+        G.aggptr[nc] = n;
+        G.segptr[nc] = (int)ttot;
+      }
+    }
+    G.keys = (uint64_t *)salloc(8ull * (ttot > 0 ? ttot : 1));
+    G.segw = (double *)salloc(8ull * (ttot > 0 ? ttot : 1));
+    if (!G.keys || !G.segw) return false;
+    if (!sync()) return false;
+    // G3: members of each aggregate
+    for (int v = tid; v < n; v += nthr) {
+      const int I = agg[v];
+      const int s = atomicAdd(&G.fill[I], 1);
+      G.members[G.aggptr[I] + s] = v;
+    }
+    if (!sync()) return false;
+    // G4: members ascending; offset of each member's entries inside its segment
+    {
+      int *s_big = sh_list();
+      int &s_nbig = sh_ints()[0];
+      for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+        if (threadIdx.x == 0) s_nbig = 0;
+        __syncthreads();
+        const int I = t0 + threadIdx.x;
+        if (I < hi) {
+          const int a = G.aggptr[I], len = G.aggptr[I + 1] - a;
+          if (len <= kSmallSeg) {
+            thread_sort(G.members + a, len);
+            int off = 0;
+            for (int k = 0; k < len; k++) {
+              const int m = G.members[a + k];
+              G.memoff[m] = off;
+              off += G.cc[m];
+            }
+          } else {
+            s_big[atomicAdd(&s_nbig, 1)] = I;
+          }
+        }
+        __syncthreads();
+        const int nbig = s_nbig;
+        for (int q = 0; q < nbig; q++) {
+          const int Ib = s_big[q];
+          const int a = G.aggptr[Ib], len = G.aggptr[Ib + 1] - a;
+          block_sort(G.members + a, len);
+          int run = 0;
+          for (int k0 = 0; k0 < len; k0 += blockDim.x) {
+            const int k = k0 + threadIdx.x;
+            const int m = k < len ? G.members[a + k] : 0;
+            const int c = k < len ? G.cc[m] : 0;
+            int tot;
+            const int ex = block_scan(c, &tot);
+            if (k < len) G.memoff[m] = run + ex;
+            run += tot;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (!sync()) return false;
+    // G5: cross entries into their aggregate's segment, key = (J, slot)
+    for (int v = tid; v < n; v += nthr) {
+      const int I = agg[v];
+      const int base = G.segptr[I];
+      int slot = G.memoff[v];
+      for (int e = rp[v]; e < rp[v + 1]; e++) {
+        const int J = agg[ci[e]];
+        if (J == I) continue;
+        G.keys[base + slot] = ((uint64_t)(uint32_t)J << 32) | (uint32_t)slot;
+        G.segw[base + slot] = wl[e];
+        slot++;
+      }
+    }
+    if (!sync()) return false;
+    // G6: sort each segment by (J, slot); distinct J per coarse row
+    red_init(red);
+    {
+      int *s_big = sh_list();
+      int &s_nbig = sh_ints()[0];
+      int &s_dist = sh_ints()[1];
+      for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+        if (threadIdx.x == 0) s_nbig = 0;
+        __syncthreads();
+        const int I = t0 + threadIdx.x;
+        if (I < hi) {
+          const int s = G.segptr[I], len = G.segptr[I + 1] - s;
+          if (len <= kSmallSeg) {
+            thread_sort(G.keys + s, len);
+            int dcount = 0;
+            for (int k = 0; k < len; k++)
+              dcount += (k == 0) || ((G.keys[s + k] >> 32) != (G.keys[s + k - 1] >> 32));
+            G.dcnt[I] = dcount;
+            red.cnt += dcount;
+          } else {
+            s_big[atomicAdd(&s_nbig, 1)] = I;
+          }
+        }
+        __syncthreads();
+        const int nbig = s_nbig;
+        for (int q = 0; q < nbig; q++) {
+          const int Ib = s_big[q];
+          const int s = G.segptr[Ib], len = G.segptr[Ib + 1] - s;
+          block_sort(G.keys + s, len);
+          if (threadIdx.x == 0) s_dist = 0;
+          __syncthreads();
+          int dc = 0;
+          for (int k = threadIdx.x; k < len; k += blockDim.x)
+            dc += (k == 0) || ((G.keys[s + k] >> 32) != (G.keys[s + k - 1] >> 32));
+          if (dc) atomicAdd(&s_dist, dc);
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            G.dcnt[Ib] = s_dist;
+            red.cnt += s_dist;
+          }
+          __syncthreads();
+        }
+      }
+    }
+    long long pre = 0;
+    if (!grid_reduce(red, &pre)) return false;
+    const long long nnzc = red.cnt;
+    int *crp = (int *)aalloc(4ull * (nc + 1));
+    int *ccol = (int *)aalloc(4ull * (nnzc > 0 ? nnzc : 1));
+    double *cw = (double *)aalloc(8ull * (nnzc > 0 ? nnzc : 1));
+    double *cd = (double *)aalloc(8ull * nc);
+    if (!crp || !ccol || !cw || !cd) return false;
+    // G7: coarse row pointers, then the summed weights in (J, slot) order
+    red_init(red);
+    {
+      long long run = pre;
+      int *s_big = sh_list();
+      int &s_nbig = sh_ints()[0];
+      for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+        if (threadIdx.x == 0) s_nbig = 0;
+        const int I = t0 + threadIdx.x;
+        const int dc = I < hi ? G.dcnt[I] : 0;
+        int tot;
+        const int ex = block_scan(dc, &tot);
+        if (I < hi) crp[I] = (int)(run + ex);
+        run += tot;
+        __syncthreads();
+        if (I < hi) {
+          const int s = G.segptr[I], len = G.segptr[I + 1] - s;
+          if (len <= kSmallSeg) {
+            int p = crp[I];
+            double dI = 0.0;
+            int k = 0;
+            while (k < len) {
+              const uint32_t J = (uint32_t)(G.keys[s + k] >> 32);
+              double sum = 0.0;
+              while (k < len && (uint32_t)(G.keys[s + k] >> 32) == J) {
+                sum += G.segw[s + (uint32_t)G.keys[s + k]];
+                k++;
+              }
+              ccol[p] = (int)J;
+              cw[p] = sum;
+              p++;
+            }
+            for (int q = crp[I]; q < p; q++) dI += cw[q];
+            cd[I] = dI;
+            red.mx = fmax(red.mx, dI);
+          } else {
+            s_big[atomicAdd(&s_nbig, 1)] = I;
+          }
+        }
+        __syncthreads();
+        const int nbig = s_nbig;
+        for (int q = 0; q < nbig; q++) {
+          const int Ib = s_big[q];
+          const int s = G.segptr[Ib], len = G.segptr[Ib + 1] - s;
+          const int p0 = crp[Ib];
+          int gr = 0;
+          for (int k0 = 0; k0 < len; k0 += blockDim.x) {
+            const int k = k0 + threadIdx.x;
+            const bool st = k < len && (k == 0 || (G.keys[s + k] >> 32) != (G.keys[s + k - 1] >> 32));
+            int tot2;
+            const int ex2 = block_scan(st ? 1 : 0, &tot2);
+            if (st) {
+              const uint32_t J = (uint32_t)(G.keys[s + k] >> 32);
+              double sum = 0.0;
+              for (int kk = k; kk < len && (uint32_t)(G.keys[s + kk] >> 32) == J; kk++)
+                sum += G.segw[s + (uint32_t)G.keys[s + kk]];
+              ccol[p0 + gr + ex2] = (int)J;
+              cw[p0 + gr + ex2] = sum;
+            }
+            gr += tot2;
+          }
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            double dI = 0.0;
+            for (int q2 = p0; q2 < p0 + gr; q2++) dI += cw[q2];
+            cd[Ib] = dI;
+            red.mx = fmax(red.mx, dI);
+          }
+          __syncthreads();
+        }
+      }
+      if (lead()) crp[nc] = (int)nnzc;
+    }
+    if (!grid_reduce(red)) return false;
+    if (lead()) {
+      Level &C = S->lv[l + 1];
+      C.n = nc;
+      C.nnz = (int)nnzc;
+      C.rowptr = crp;
+      C.col = ccol;
+      C.w64 = cw;
+      C.w32 = nullptr;
+      C.d = cd;
+      C.sigma = 2.0 * red.mx;
+      C.agg = nullptr;
+      C.mate = nullptr;
+      C.nc = 0;
+    }
+    if (!sync()) return false;
+    mark(PH_GALERKIN, 40.0 * n + (12.0 + 8.0 + 16.0 * 3.0) * L->nnz);
+    return true;
+  }
+
+  // ---- A7: coarsest level: connectivity, random start ---------------------
+  FZD bool coarsest_solve(int J) {
+    Level *L = &S->lv[J];
+    const int n = L->n;
+    const int *rp = L->rowptr, *ci = L->col, *iperm = L->iperm;
+    soff = 0;
+    int *lab = (int *)salloc(4ull * n);
+    if (!lab) return false;
+    for (int v = tid; v < n; v += nthr) lab[v] = v;
+    if (!sync()) return false;
+    for (int it = 0;; it++) {
+      Red red;
+      red_init(red);
+      for (int v = tid; v < n; v += nthr) {
+        int m = lab[v];
+        for (int e = rp[v]; e < rp[v + 1]; e++) m = min(m, lab[ci[e]]);
+        if (m < lab[v]) {
+          lab[v] = m;
+          red.cnt++;
+        }
+      }
+      if (!grid_reduce(red)) return false;
+      if (red.cnt == 0) break;
+      if (it > n) {
+        fail(ST_EINVAL);
+        return false;
+      }
+    }
+    {
+      Red red;
+      red_init(red);
+      for (int v = tid; v < n; v += nthr) red.cnt += lab[v] != 0;
+      if (!grid_reduce(red)) return false;
+      if (red.cnt != 0) {
+        fail(ST_EDISC);
+        return false;
+      }
+    }
+    T *x = (T *)L->x;
+    Red red;
+    red_init(red);
+    const uint64_t seed = S->opt.seed;
+    for (int i = tid; i < n; i += nthr) {
+      const T v = (T)uniform01(seed, (uint64_t)i);
+      x[iperm[i]] = v;
+      red.s[0] += (double)v;
+      red.s[1] += (double)v * (double)v;
+    }
+    if (!grid_reduce(red)) return false;
+    const double mu = red.s[0] / n, var = red.s[1] - red.s[0] * mu;
+    const double g = S->opt.guard;
+    if (!(var > g * g)) {
+      fail(ST_EDEGEN);
+      return false;
+    }
+    mark(PH_COARSEST, 16.0 * n + 8.0 * L->nnz);
+    return smooth(J, S->opt.pi_max_iters_coarsest, mu, 1.0 / sqrt(var), PH_COARSEST);
+  }
+
+  // ---- A8: prolongation y^j = I^T y^{j+1} ----------------------------------
+  FZD bool prolong(int l) {
+    Level *F = &S->lv[l];
+    const Level *Cl = &S->lv[l + 1];
+    const int n = F->n;
+    const T *xc = (const T *)Cl->x;
+    const T muc = (T)Cl->mu, sc = (T)Cl->s;
+    T *x = (T *)F->x;
+    const int *sagg = F->sagg;
+    Red red;
+    red_init(red);
+    for (int k = tid; k < n; k += nthr) {
+      const T v = (xc[sagg[k]] - muc) * sc;
+      x[k] = v;
+      red.s[0] += (double)v;
+      red.s[1] += (double)v * (double)v;
+    }
+    if (!grid_reduce(red)) return false;
+    const double mu = red.s[0] / n, var = red.s[1] - red.s[0] * mu;
+    const double g = S->opt.guard;
+    if (!(var > g * g)) {
+      fail(ST_EDEGEN);
+      return false;
+    }
+    mark(PH_PROLONG, (4.0 + 2.0 * sizeof(T)) * n);
+    return smooth(l, S->opt.pi_max_iters, mu, 1.0 / sqrt(var), PH_GS);
+  }
+
+  // ---- A9 + A10: Gauss-Seidel sweeps, then shifted power iteration ----------
+  FZD bool smooth(int l, int kmax, double mu, double s, int gs_phase) {
+    Level *L = &S->lv[l];
+    const int n = L->n, nnz = L->nnz, C = L->ncolors;
+    const int *srp = L->srowptr, *scol = L->scol, *cst = L->colstart;
+    const T *sw = (const T *)L->sw;
+    T *A = (T *)L->x, *B = (T *)L->y;
+    const double g = S->opt.guard;
+    const double sweep_bytes = 4.0 * (n + 1) + (4.0 + sizeof(T)) * nnz + 2.0 * sizeof(T) * n;
+    int sweeps = 0;
+    for (int k = 0; k < S->opt.gs_sweeps; k++) {
+      Red red;
+      red_init(red);
+      const T muT = (T)mu, sT = (T)s;
+      for (int c = 0; c < C; c++) {
+        const int cs = cst[c], ce = cst[c + 1];
+        for (int i = cs + tid; i < ce; i += nthr) {
+          T acc = (T)0, dsum = (T)0;
+          const int e1 = srp[i + 1];
+          for (int e = srp[i]; e < e1; e++) {
+            const int j = scol[e];
+            const T wv = sw[e];
+            const T xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
+            acc += wv * xj;
+            dsum += wv;
+          }
+          const T xi = acc / dsum;
+          B[i] = xi;
+          red.s[0] += (double)xi;
+          red.s[1] += (double)xi * (double)xi;
+        }
+        if (c + 1 < C && !sync()) return false;
+      }
+      if (!grid_reduce(red)) return false;
+      mark(gs_phase == PH_COARSEST ? PH_COARSEST : PH_GS, sweep_bytes);
+      const double m2 = red.s[0] / n, var = red.s[1] - red.s[0] * m2;
+      if (!(var > g * g)) break;  // the sweep annihilated the iterate: keep the previous one
+      T *t = A;
+      A = B;
+      B = t;
+      mu = m2;
+      s = 1.0 / sqrt(var);
+      sweeps++;
+    }
+    const double sigma = L->sigma;
+    const double tol = S->opt.pi_cos_tol, rtol = S->opt.resid_tol;
+    const bool resid = rtol > 0.0;
+    int done = 0, capped = 0;
+    double lastc = 0.0;
+    for (int it = 1; it <= kmax; it++) {
+      Red red;
+      red_init(red);
+      const T muT = (T)mu, sT = (T)s, sigT = (T)sigma;
+      for (int i = tid; i < n; i += nthr) {
+        const T xi = A[i];
+        T acc = (T)0;
+        const int e1 = srp[i + 1];
+        for (int e = srp[i]; e < e1; e++) acc += sw[e] * (xi - A[scol[e]]);
+        const T xh = (xi - muT) * sT;
+        const T yi = sigT * xh - sT * acc;
+        B[i] = yi;
+        const double yd = (double)yi, xd = (double)xh;
+        red.s[0] += yd;
+        red.s[1] += yd * yd;
+        red.s[2] += yd * xd;
+        red.s[3] += xd;
+        if (resid) {
+          const double lx = (double)sT * (double)acc;
+          red.s[4] += lx * lx;
+          red.s[5] += xd * lx;
+        }
+      }
+      if (!grid_reduce(red)) return false;
+      mark(gs_phase == PH_COARSEST ? PH_COARSEST : PH_PI, sweep_bytes);
+      const double my = red.s[0] / n, var = red.s[1] - red.s[0] * my;
+      if (!(var > (g * sigma) * (g * sigma))) break;  // vanished: keep the previous vector
+      const double sy = 1.0 / sqrt(var);
+      const double cosv = (red.s[2] - my * red.s[3]) * sy;
+      double rr = 0.0;
+      if (resid) rr = sqrt(fmax(red.s[4] - red.s[5] * red.s[5], 0.0));
+      T *t = A;
+      A = B;
+      B = t;
+      mu = my;
+      s = sy;
+      lastc = cosv;
+      done = it;
+      if (cosv > 1.0 - tol && (!resid || rr <= rtol * sigma)) break;
+      if (it == kmax) capped = 1;
+    }
+    if (lead()) {
+      L->x = A;
+      L->y = B;
+      L->mu = mu;
+      L->s = s;
+      L->gs_sweeps = sweeps;
+      L->pi_iters = done;
+      L->last_cos = lastc;
+      L->capped = capped;
+    }
+    return sync();
+  }
+
+  // ---- A11: Rayleigh quotient, residual, orthogonality, sign, output --------
+  FZD bool finalize() {
+    Level *L = &S->lv[0];
+    const int n = L->n, nnz = L->nnz;
+    const int *srp = L->srowptr, *scol = L->scol, *perm = L->perm, *iperm = L->iperm;
+    const T *sw = (const T *)L->sw;
+    const T *A = (const T *)L->x;
+    const double mu = L->mu, s = L->s;
+    Red red;
+    red_init(red);
+    for (int k = tid; k < n; k += nthr) {
+      const double xk = ((double)A[k] - mu) * s;
+      double lx = 0.0, num = 0.0;
+      const int e1 = srp[k + 1];
+      for (int e = srp[k]; e < e1; e++) {
+        const double dl = xk - ((double)A[scol[e]] - mu) * s;
+        const double wv = (double)sw[e];
+        lx += wv * dl;
+        num += wv * dl * dl;
+      }
+      red.s[0] += xk * xk;
+      red.s[1] += xk;
+      red.s[2] += num;
+      red.s[3] += lx * lx;
+      const double ax = fabs(xk);
+      const int oi = perm[k];
+      if (ax > red.mx || (ax == red.mx && oi < red.mxi)) {
+        red.mx = ax;
+        red.mxi = oi;
+      }
+    }
+    if (!grid_reduce(red)) return false;
+    const double xx = red.s[0];
+    const double lam = red.s[2] / (2.0 * xx);
+    const double r2 = red.s[3] / xx - lam * lam;
+    const double xbig = ((double)A[iperm[red.mxi]] - mu) * s;
+    const double sign = xbig < 0.0 ? -1.0 : 1.0;
+    const double inv = sign / sqrt(xx);
+    double *out = S->xout;
+    if (out)
+      for (int k = tid; k < n; k += nthr) out[perm[k]] = ((double)A[k] - mu) * s * inv;
+    int ptot = 0, gtot = 0, cap = 0;
+    for (int l = 0; l < nlevels; l++) {
+      ptot += S->lv[l].pi_iters;
+      gtot += S->lv[l].gs_sweeps;
+      cap |= S->lv[l].capped;
+    }
+    if (lead()) {
+      S->lambda = lam;
+      S->residual = sqrt(fmax(r2, 0.0));
+      S->ortho = fabs(red.s[1]) / (sqrt((double)n) * sqrt(xx));
+      S->pi_total = ptot;
+      S->gs_total = gtot;
+      S->capped = cap;
+    }
+    if (!sync()) return false;
+    mark(PH_FINAL, 4.0 * (n + 1) + (4.0 + sizeof(T)) * nnz + (2.0 * sizeof(T) + 8.0 + 8.0) * n);
+    return true;
+  }
+
+  // ---- the walk over the hierarchy ------------------------------------------
+  // mode 0: setup only; 1: everything eligible; 2: solve only
+  FZD bool run(int mode) {
+    if (status() != 0) return false;
+    if (mode != 2) {
+      if (nlevels == 0) {
+        if (!elig(S->n0)) return true;
+        if (!ingest()) return false;
+        nlevels = 1;
+        persist();
+      }
+      while (!setup_done) {
+        const int l = nlevels - 1;
+        const int n = S->lv[l].n;
+        if (!elig(n)) return true;
+        if (!colour(l)) return false;
+        if (!reorder(l)) return false;
+        if (n <= S->opt.coarse_max_n || nlevels >= S->opt.max_levels) {
+          setup_done = 1;
+          coarsest = l;
+          persist();
+          break;
+        }
+        if (!match(l)) return false;
+        GalerkinScratch G;
+        int nc = -1;
+        if (!aggregate(l, nc, G)) return false;
+        if (nc < 0) {
+          setup_done = 1;
+          coarsest = l;
+          persist();
+          break;
+        }
+        if (!galerkin(l, nc, G)) return false;
+        nlevels++;
+        persist();
+      }
+    }
+    if (mode == 0) return true;
+    if (!setup_done) return true;
+    if (!coarsest_solved) {
+      if (!elig(S->lv[coarsest].n)) return true;
+      if (!coarsest_solve(coarsest)) return false;
+      coarsest_solved = 1;
+      solved = coarsest;
+      persist();
+    }
+    while (solved > 0) {
+      const int l = solved - 1;
+      if (!elig(S->lv[l].n)) return true;
+      if (!prolong(l)) return false;
+      solved = l;
+      persist();
+    }
+    if (!finalized) {
+      if (!finalize()) return false;
+      finalized = 1;
+      persist();
+    }
+    return true;
+  }
+};
+
+// fault injection for the bounded-wait test: block 0 leaves before the first
+// barrier, so every other block's wait runs out and reports ETIMEOUT
+template <class T, bool GRID>
+FZD void engine_entry(State *S, int mode) {
+  if (GRID && S->opt.fault_inject == 1 && blockIdx.x == 0) return;
+  Eng<T, GRID> E;
+  E.init(S);
+  E.run(mode);
+  E.persist();
+}
+
+}  // namespace fz

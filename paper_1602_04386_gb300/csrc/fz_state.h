@@ -1,0 +1,119 @@
+// fz_state.h -- device-resident solve state shared by the host driver and the
+// engine kernels.  One State lives in device memory per plan; the host writes
+// its header before a solve and reads it back afterwards.  Level descriptors
+// are filled on the device as the hierarchy is built (no host round trips).
+#pragma once
+#include <stdint.h>
+
+namespace fz {
+
+constexpr int kMaxLevels = 32;
+constexpr int kMaxBlocks = 2048;   // grid-wide kernel blocks (partials buffer size)
+constexpr int kMaxColors = 1024;   // colour classes per level supported by the reorder
+constexpr int kCtaThreads = 1024;  // one-block kernel
+constexpr int kGridThreads = 512;  // grid-wide kernel block size
+
+enum Phase {
+  PH_INGEST = 0, PH_COLOR, PH_REORDER, PH_MATCH, PH_AGG, PH_GALERKIN,
+  PH_COARSEST, PH_PROLONG, PH_GS, PH_PI, PH_FINAL, PH_COUNT
+};
+
+// internal status codes; the host maps them to fiedler_status
+enum : int {
+  ST_OK = 0, ST_EINVAL = -1, ST_ENOMEM = -2, ST_EDISC = -3, ST_ENOTCONV = -4, ST_ETIMEOUT = -5,
+  ST_EDEGEN = -8, ST_ENOTSUP = -9, ST_ARENA = -100, ST_SCRATCH = -101
+};
+
+struct Opts {
+  int precision;
+  int coarse_max_n;
+  int max_levels;
+  int gs_sweeps;
+  int pi_max_iters;
+  int pi_max_iters_coarsest;
+  int tie_rule;
+  int validate;
+  int tail_max_n;
+  int fault_inject;
+  double stall_ratio;
+  double pi_cos_tol;
+  double resid_tol;
+  double guard;              // annihilation guard of the deflated norm
+  unsigned long long seed;
+  unsigned long long barrier_timeout_ns;
+};
+
+struct Level {
+  // setup operator in the graph's own numbering (off-diagonal CSR, FP64 or
+  // the caller's float weights on the fine level), diagonal and shift
+  int n, nnz;
+  int *rowptr, *col;
+  double *w64;
+  float *w32;
+  double *d;
+  double sigma;
+  // heavy-edge matching and aggregate map to the next level
+  int *mate, *agg;
+  int nc;
+  // colouring; perm[k] = vertex at solve position k, iperm its inverse
+  int *color, *colstart, *perm, *iperm;
+  int ncolors;
+  // solve operator in colour order (value type float or double)
+  int *srowptr, *scol;
+  void *sw;
+  int *sagg;  // solve position on this level -> solve position on the next
+  // iterate: x (or y) with a lazy affine map xhat = (x - mu) * s
+  void *x, *y;
+  double mu, s;
+  // counters
+  int match_rounds, color_rounds, gs_sweeps, pi_iters, capped;
+  double last_cos;
+};
+
+struct Red {               // per-block partials of a grid reduction (72 bytes)
+  double s[6];
+  double mx;
+  long long cnt;
+  int mxi;
+  int pad;
+};
+
+struct State {
+  int status;
+  int setup_done;
+  long long bad_index;
+  int nlevels;
+  int coarsest;
+  int coarsest_solved;
+  int solved;              // lowest level index whose vector is final
+  int finalized;
+  int capped;
+  Opts opt;
+  // input graph
+  int n0, nnz0;
+  const int *in_rowptr, *in_col;
+  const void *in_w;
+  int in_w_f64;
+  int pad1;
+  // device arenas (bump allocation, offsets advanced identically by every block)
+  char *arena;
+  unsigned long long arena_size, arena_off;
+  char *scratch;
+  unsigned long long scratch_size;
+  double *xout;            // device output (n0 doubles), original numbering
+  Red *part;               // [2][kMaxBlocks] partials
+  // results
+  double lambda, residual, ortho;
+  int pi_total, gs_total;
+  // grid barrier: arrival count, generation, verdict of the last completed barrier
+  unsigned bar_count, bar_gen;
+  int bar_ok;
+  int pad2;
+  // device-timer profile: [0] grid-wide kernel, [1] one-block kernel
+  unsigned long long t_last;
+  double phase_ns[2][PH_COUNT];
+  double phase_bytes[2][PH_COUNT];
+  Level lv[kMaxLevels];
+};
+
+}  // namespace fz

@@ -1,0 +1,14 @@
+// kernels.h -- host-visible handles of the engine kernels (one set per value type)
+#pragma once
+#include "fz_state.h"
+
+namespace fz {
+struct KernelSet {
+  const void *grid_setup;  // cooperative, kGridThreads per block: setup of levels with n > tail_max_n
+  const void *grid_solve;  // cooperative, kGridThreads per block: solve of levels with n > tail_max_n
+  const void *cta;         // one block of kCtaThreads: everything on levels with n <= tail_max_n
+  const char *names[3];
+};
+void kernels_f32(KernelSet *k);
+void kernels_f64(KernelSet *k);
+}  // namespace fz

@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol that
+include/fiedler.h declares; the ctypes structs match the header's layout."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1602_04386_gb300 import build, fiedler
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fiedler.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return fiedler.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fiedler_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_what_the_binding_lists():
+    assert declared_functions() == sorted(fiedler.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_calls_that_need_no_gpu(lib):
+    o = fiedler.fiedler_options_default()
+    assert o.coarse_max_n == 25 and o.pi_cos_tol == 1e-6 and o.gs_sweeps == 2
+    assert o.precision == fiedler.FIEDLER_FP32_FP64RED and o.max_levels == 30
+    assert fiedler.fiedler_status_str(fiedler.FIEDLER_EDISCONNECTED) == "graph is not connected"
+    assert fiedler.fiedler_plan_num_levels(None) == 0
+    st, _ = fiedler.fiedler_plan_level_info(None, 0)
+    assert st == fiedler.FIEDLER_EINVAL
+
+
+def _offsets(struct):
+    return [getattr(struct, f[0]).offset for f in struct._fields_]
+
+
+def test_struct_layouts_match_header():
+    # sizes computed by the C compiler from the header itself
+    import subprocess
+    import tempfile
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "fiedler.h"
+int main(void){
+ printf("%zu %zu %zu %zu %zu\n", sizeof(fiedler_options), sizeof(fiedler_graph), sizeof(fiedler_result),
+        sizeof(fiedler_level_info), sizeof(fiedler_profile));
+ printf("%zu %zu %zu %zu\n", offsetof(fiedler_options, seed), offsetof(fiedler_result, x),
+        offsetof(fiedler_result, bad_index), offsetof(fiedler_profile, phase_bytes));
+ return 0;}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe])
+        out = subprocess.check_output([exe]).decode().split()
+    sizes = [int(v) for v in out[:5]]
+    offs = [int(v) for v in out[5:]]
+    assert sizes == [C.sizeof(fiedler.fiedler_options), C.sizeof(fiedler.fiedler_graph),
+                     C.sizeof(fiedler.fiedler_result), C.sizeof(fiedler.fiedler_level_info),
+                     C.sizeof(fiedler.fiedler_profile)]
+    assert offs == [fiedler.fiedler_options.seed.offset, fiedler.fiedler_result.x.offset,
+                    fiedler.fiedler_result.bad_index.offset, fiedler.fiedler_profile.phase_bytes.offset]
