@@ -42,7 +42,12 @@
  *       vector is deflated and the iterate normalised after every sweep.  Order:
  *       lexicographic (gs_order 0) or colour classes ascending, ascending index
  *       within a class (gs_order 1).  A sweep whose deflated result has norm
- *       <= guard is discarded and ends the smoothing on that level.
+ *       <= guard (2^-20; the input is a unit vector) is discarded and ends the
+ *       smoothing on that level.  The guard sits above the rounding noise of a
+ *       deflated norm taken as sum x^2 - (sum x)^2 / n in double, so that an
+ *       implementation fusing the deflation into its reductions takes the same
+ *       decision; it only fires when a sweep maps the iterate onto the constant
+ *       vector (K_2, stars swept centre first).
  *   R6  after the Gauss-Seidel sweeps every level runs power iteration on
  *       sigma I - L, sigma = 2 max_i d_i (Gershgorin), with deflation and
  *       normalisation, until (u^k, u^{k-1}) > 1 - pi_cos_tol and (if
@@ -109,7 +114,7 @@ typedef struct {
   int pi_max_iters_coarsest; /* cap on the coarsest level */
   double pi_cos_tol;         /* 1e-6 (Sec. 3) */
   double resid_tol;          /* 0 = paper stop rule only */
-  double guard;              /* annihilation guard, 2^-40 */
+  double guard;              /* annihilation guard, 2^-20 */
   uint64_t seed;             /* random start on the coarsest level */
   int coarsest_dense;        /* 1 = coarsest eigenvector by dense Jacobi */
 } oracle_opts;
@@ -190,7 +195,7 @@ void oracle_default_opts(oracle_opts *o) {
   o->pi_max_iters_coarsest = 100000;
   o->pi_cos_tol = 1e-6;
   o->resid_tol = 0.0;
-  o->guard = 9.094947017729282e-13; /* 2^-40 */
+  o->guard = 9.5367431640625e-07; /* 2^-20 */
   o->seed = 20160214ULL;
   o->coarsest_dense = 0;
 }

@@ -181,7 +181,9 @@ fiedler_status run_solve(fiedler_plan *p, int64_t n, int64_t nnz, const int32_t 
     o.stall_ratio = p->opt.stall_ratio;
     o.pi_cos_tol = p->opt.pi_cos_tol;
     o.resid_tol = p->opt.resid_tol;
-    o.guard = type == 0 ? ldexp(1.0, -40) : ldexp(1.0, -16);
+    // annihilation guard on the deflated norm of a unit vector: above the
+    // rounding noise of the fused variance sum x^2 - (sum x)^2 / n
+    o.guard = type == 0 ? ldexp(1.0, -20) : ldexp(1.0, -16);
     o.seed = p->opt.seed;
     o.barrier_timeout_ns = (unsigned long long)p->opt.barrier_timeout_ms * 1000000ull;
     h->bad_index = LLONG_MAX;

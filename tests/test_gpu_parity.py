@@ -71,9 +71,12 @@ def compare(g, precision, lam_tol, x_tol=None, **kw):
         x = ref.x(g.n)
         if x_tol is not None:
             assert np.abs(r.x - x).max() <= x_tol
-        # the oracle's own stop rule gives the same counts unless a cos test sat on the threshold
-        free = oracle.solve(g, **okw)
-        if free.pi_iters != counts:
+        # FP64 form: the oracle's own stop rule gives the same counts unless a cos
+        # test sat on the threshold.  (The FP32 form takes its stop decisions on
+        # float iterates, so its counts may differ; the comparison above replays
+        # the oracle with the GPU's counts.)
+        free = oracle.solve(g, **okw) if precision == FP64 else None
+        if free is not None and free.pi_iters != counts:
             for l, (a, b) in enumerate(zip(free.pi_iters, counts)):
                 if a != b:
                     assert abs(ref.level(l).last_cos - (1 - 1e-6)) < 1e-9 or abs(
