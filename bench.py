@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 cascadic multigrid Fiedler solver.
+
+One step = one whole solve (ingest + setup of the hierarchy + coarsest solve +
+cascadic refinement + Rayleigh quotient) of the linear-complexity-sweep
+workload's largest graph: a 2048 x 1536 5-point grid with f32 edge weights
+0.5 + U[0,1) from the seeded splitmix64 stream, in the FP32 form (float values
+and matvec, double reductions).  Inputs are resident in HBM for `value`; `e2e`
+times the same solve through the C-ABI with pinned host inputs and a host
+output vector.  The working set (~0.9 GB) exceeds L2 and L2 is also flushed
+between steps (256 MiB write outside the timed events).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank solves its own replica (graphs are independent,
+no collective on the data path); value = solves of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1602_04386_gb300 import inputs  # noqa: E402
+
+METRIC = "Fiedler solves/s & SpMV/GS HBM GB/s at lambda2 rel err <=1e-5 vs plain; p50/p99 ms"
+WORKLOAD = dict(m=2048, k=1536, weights="uniform", seed=inputs.BASE_SEED + 2)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_name(w=WORKLOAD):
+    return f"grid{w['m']}x{w['k']}-{w['weights']}-seed{w['seed']}"
+
+
+def make_graph(w=WORKLOAD):
+    return inputs.grid(w["m"], w["k"], w["weights"], seed=w["seed"])
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def engine_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1602_04386_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    if the summary is missing or was taken on different engine sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("engine_sources") != engine_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step solves a quarter-size
+    sample of the workload (1024 x 768 grid of the same family) and is scaled to
+    the full workload by its nonzero count (the method is linear in the graph size)."""
+    import oracle
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    full = make_graph()
+    samp_w = dict(WORKLOAD, m=WORKLOAD["m"] // 2, k=WORKLOAD["k"] // 2)
+    g = make_graph(samp_w)
+    scale = full.nnz / g.nnz
+    for _ in range(args.warmup):
+        oracle.solve(g)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.solve(g)
+        t.append(time.perf_counter() - t0)
+        assert r.status == 0
+    sec_full = statistics.mean(t) * scale
+    value = 1.0 / sec_full
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_full * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(), "n": full.n, "nnz": full.nnz},
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "solves/s", "cores": 1,
+                         "sample": f"{workload_name(samp_w)} per step (nnz {g.nnz}), time x {scale:.3f} "
+                                   f"(nnz ratio to the full workload)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp64 / cpu baseline legs (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not args.no_extras:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1602_04386_gb300 import fiedler
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    # a dedicated stream: the plan launches on it and the step events are recorded on it
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    prec = fiedler.FIEDLER_FP32_FP64RED if args.precision == "fp32" else fiedler.FIEDLER_FP64
+
+    g = make_graph()
+    gs, keep = fiedler.device_graph(g, dev)
+    x = torch.empty(g.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    plan = fiedler.Plan(stream=stream.cuda_stream, precision=prec)
+
+    def solve_once():
+        r = plan.solve_struct(gs, x, x_on_device=True)
+        if r.status != fiedler.FIEDLER_OK:
+            raise fiedler.FiedlerError(r.status, "fiedler_solve")
+        return r
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        solve_once()
+    plan.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kms = {}
+    kbytes = {}
+    klaunch = {}
+    ph_ms = np.zeros((2, 16))
+    ph_bytes = np.zeros((2, 16))
+    launches = 0
+    res = None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            res = solve_once()
+            ev[i][1].record(stream)
+            pr = plan.profile()
+            launches += int(pr.kernel_launches)
+            for k in range(pr.n_kernels):
+                name = pr.kernel_name[k].decode()
+                if pr.kernel_launches_by[k]:
+                    kms[name] = kms.get(name, 0.0) + pr.kernel_ms[k]
+                    kbytes[name] = kbytes.get(name, 0.0) + pr.kernel_bytes[k]
+                    klaunch[name] = klaunch.get(name, 0) + pr.kernel_launches_by[k]
+            ph_ms += np.array([[pr.phase_ms[a][b] for b in range(16)] for a in range(2)])
+            ph_bytes += np.array([[pr.phase_bytes[a][b] for b in range(16)] for a in range(2)])
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    plan.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = ws * args.steps / (tot_ms / 1e3)
+
+    # roofline of the dominant kernel (most device time in the timed steps)
+    peak, peak_kind = measured_peaks()
+    dom = max(kms, key=lambda k: kms[k])
+    achieved = kbytes[dom] / (kms[dom] / 1e3) / 1e9
+    phase_names = [pr.phase_name[i].decode() for i in range(pr.n_phases)]
+    gi, pi_ = phase_names.index("gauss_seidel"), phase_names.index("power_iter")
+    sg_bytes = ph_bytes[0][gi] + ph_bytes[0][pi_]
+    sg_ms = ph_ms[0][gi] + ph_ms[0][pi_]
+    spmv_gs_gbs = sg_bytes / (sg_ms / 1e3) / 1e9 if sg_ms > 0 else None
+    phases = {f"{'grid' if a == 0 else 'cta'}.{phase_names[b]}": round(ph_ms[a][b] / args.steps, 4)
+              for a in range(2) for b in range(pr.n_phases) if ph_ms[a][b] > 0}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == fiedler.FIEDLER_FP32_FP64RED else "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(), "n": g.n, "nnz": g.nnz, "edges": g.nnz // 2,
+                   "form": "FP32 values/matvec, FP64 reductions" if prec else "FP64",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "flushed between steps (256 MiB write outside the timed events); working set > L2"},
+        "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+        "wall_s": wall,
+        "lambda2": res.lambda2, "residual": res.residual, "levels": res.levels,
+        "spmv_gs_hbm_gbs": spmv_gs_gbs,
+        "edge_sweeps_per_s": None,
+        "gpu_launches": launches,
+        "kernels": {k: {"launches": klaunch[k], "ms_per_step": kms[k] / args.steps,
+                        "gbs": kbytes[k] / (kms[k] / 1e3) / 1e9 if kms[k] > 0 else None} for k in kms},
+        "phase_ms_per_step": phases,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
+                     "traffic": ncu_traffic(dom), "algorithmic_bytes_per_launch": kbytes[dom] / klaunch[dom]},
+    }
+    # edge-sweeps: nnz (= 2E) entries per Gauss-Seidel sweep or power-iteration matvec, all levels
+    sweeps = 0
+    for l in range(plan.num_levels):
+        li = plan.level_info(l)
+        sweeps += int(li.nnz) * (li.gs_sweeps + li.pi_iters)
+    line["edge_sweeps_per_s"] = ws * sweeps / (ms_per_step / 1e3)
+    line["levels_n_ncolors_mrounds_crounds_gs_pi"] = [
+        [int(li.n), li.ncolors, li.match_rounds, li.color_rounds, li.gs_sweeps, li.pi_iters]
+        for li in (plan.level_info(l) for l in range(plan.num_levels))]
+    # device time per level (last timed step), phases with > 1 us
+    line["level_phase_us"] = [
+        {phase_names[i]: round(li.phase_ms[i] * 1e3, 1) for i in range(len(phase_names)) if li.phase_ms[i] > 1e-3}
+        for li in (plan.level_info(l) for l in range(plan.num_levels))]
+    clocks = clk.summary()
+    if clocks is not None:
+        line["clocks"] = clocks
+
+    if not args.no_extras:
+        # accuracy against the plain FP64 form, and its throughput
+        plan64 = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP64)
+        x64 = torch.empty_like(x)
+        r64 = None
+        t64 = []
+        for i in range(3 + 5):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r64 = plan64.solve_struct(gs, x64, x_on_device=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 3:
+                t64.append(e0.elapsed_time(e1))
+        plan64.close()
+        line["lambda2_fp64_plain"] = r64.lambda2
+        line["lambda2_rel_err_vs_fp64"] = abs(res.lambda2 - r64.lambda2) / abs(r64.lambda2)
+        line["fp64_plain_solves_per_s"] = 1e3 / statistics.mean(t64)
+        # end to end through the C-ABI: pinned host inputs, host output vector
+        hrp = torch.from_numpy(g.rowptr).pin_memory().numpy()
+        hci = torch.from_numpy(g.col).pin_memory().numpy()
+        hw = torch.from_numpy(g.w).pin_memory().numpy()
+        hx = torch.empty(g.n, dtype=torch.float64).pin_memory().numpy()
+        hg = fiedler.fiedler_graph(g.n, g.nnz, hrp.ctypes.data, hci.ctypes.data, hw.ctypes.data,
+                                   fiedler.FIEDLER_W_F32, 0)
+        e2e_t = []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rr = plan.solve_struct(hg, hx, x_on_device=False)
+            t1 = time.perf_counter()
+            if rr.status != fiedler.FIEDLER_OK:
+                raise fiedler.FiedlerError(rr.status, "fiedler_solve (host inputs)")
+            if i >= args.warmup:
+                e2e_t.append(t1 - t0)
+        e2e_s = statistics.mean(e2e_t)
+        if dist is not None:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        line["e2e"] = {"value": ws / e2e_s, "unit": "solves/s",
+                       "h2d_bytes_per_step": int(hrp.nbytes + hci.nbytes + hw.nbytes),
+                       "d2h_bytes_per_step": int(hx.nbytes)}
+        if rank == 0 and ws == 1:
+            import oracle
+            nrep = 2
+            t0 = time.perf_counter()
+            for _ in range(nrep):
+                ro = oracle.solve(g)
+            tc = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": nrep / tc, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"{nrep} whole solves of {workload_name()} (single-threaded C)",
+                                    "lambda2": ro.lam}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

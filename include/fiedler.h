@@ -165,6 +165,8 @@ typedef struct {
   int pi_iters;              /* power iterations on this level */
   double sigma;              /* shift: 2 max_i d_i */
   double last_cos;           /* (u^k, u^{k-1}) of the last power iteration */
+  float phase_ms[16];        /* device time spent on this level per phase, in the order of
+                                fiedler_profile.phase_name (device timer) */
 } fiedler_level_info;
 
 /* Number of levels of the last solve (0 before any solve). */

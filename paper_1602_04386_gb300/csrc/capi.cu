@@ -52,7 +52,8 @@ struct fiedler_plan {
   int grid_blocks[2][2];    // [type][setup/solve]
   State *d_state = nullptr;
   State *h_state = nullptr; // pinned mirror
-  fz::Red *d_part = nullptr;
+  fz::IRed *d_ipart = nullptr;
+  double *d_dpart = nullptr;
   char *d_arena = nullptr;
   size_t arena_cap = 0;
   char *d_scratch = nullptr;
@@ -118,7 +119,11 @@ size_t arena_estimate(int64_t n, int64_t nnz, size_t tsz, bool wf64) {
 }
 
 size_t scratch_estimate(int64_t n, int64_t nnz, int nblocks) {
-  double b = 4.0 * n * 2 + 4.0 * fz::kMaxColors * nblocks + 4.0 * n * 3 + 4.0 * (n + 1) * 6 + 16.0 * nnz +
+  // colouring: cround + 3 worklists + colour histogram; matching: cand + 3
+  // worklists (both released before the Galerkin scratch is taken, but sized
+  // together for simplicity); Galerkin: 9 per-vertex/per-aggregate arrays and
+  // (J, slot) keys + FP64 weights per cross entry
+  double b = 4.0 * n * 4 + 4.0 * fz::kMaxColors * nblocks + 4.0 * n * 4 + 4.0 * (n + 1) * 9 + 16.0 * nnz +
              64.0 * 256.0 + (1 << 20);
   return (size_t)b;
 }
@@ -198,7 +203,8 @@ fiedler_status run_solve(fiedler_plan *p, int64_t n, int64_t nnz, const int32_t 
     h->scratch = p->d_scratch;
     h->scratch_size = p->scratch_cap;
     h->xout = x_dev;
-    h->part = p->d_part;
+    h->ipart = p->d_ipart;
+    h->dpart = p->d_dpart;
     memset(&p->prof, 0, sizeof(p->prof));
     CK(cudaMemcpyAsync(p->d_state, h, sizeof(State), cudaMemcpyHostToDevice, p->stream));
     CK(cudaEventRecord(p->ev[0], p->stream));
@@ -438,7 +444,9 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
     }
   }
   if (cudaMalloc(&p->d_state, sizeof(State)) != cudaSuccess) return fail(FIEDLER_ENOMEM);
-  if (cudaMalloc(&p->d_part, sizeof(fz::Red) * 2 * fz::kMaxBlocks) != cudaSuccess) return fail(FIEDLER_ENOMEM);
+  if (cudaMalloc(&p->d_ipart, sizeof(fz::IRed) * 2 * fz::kMaxBlocks) != cudaSuccess) return fail(FIEDLER_ENOMEM);
+  if (cudaMalloc(&p->d_dpart, sizeof(double) * 2 * fz::kMaxBlocks * fz::kDSum) != cudaSuccess)
+    return fail(FIEDLER_ENOMEM);
   if (cudaMallocHost(&p->h_state, sizeof(State)) != cudaSuccess) return fail(FIEDLER_ENOMEM);
   for (int i = 0; i < 8; i++)
     if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return fail(FIEDLER_ECUDA);
@@ -546,7 +554,8 @@ void fiedler_plan_destroy(fiedler_plan *p) {
   if (p->d_xout) cudaFreeAsync(p->d_xout, p->stream);
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->d_state) cudaFree(p->d_state);
-  if (p->d_part) cudaFree(p->d_part);
+  if (p->d_ipart) cudaFree(p->d_ipart);
+  if (p->d_dpart) cudaFree(p->d_dpart);
   if (p->h_state) cudaFreeHost(p->h_state);
   for (int i = 0; i < 8; i++)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
@@ -589,6 +598,7 @@ fiedler_status fiedler_plan_level_info(const fiedler_plan *p, int l, fiedler_lev
   info->pi_iters = L.pi_iters;
   info->sigma = L.sigma;
   info->last_cos = L.last_cos;
+  for (int i = 0; i < 16; i++) info->phase_ms[i] = i < fz::PH_COUNT ? (float)(p->h_state->level_ns[l][i] * 1e-6) : 0.f;
   return FIEDLER_OK;
 }
 

@@ -12,12 +12,19 @@
 //
 // The same code runs in two shapes.  GRID = true: a cooperative launch over
 // all SMs, phases separated by a bounded grid barrier, for levels with
-// n > tail_max_n.  GRID = false: one 1024-thread block with __syncthreads, for
-// the small levels at the bottom of the hierarchy, where grid barriers would
-// dominate.  Every thread of every block runs the same control flow: decisions
-// are taken from grid reductions that every block finishes redundantly (same
-// data, same order, same result), and arena offsets are advanced identically
-// by every thread, so no extra barrier is needed to publish them.
+// n > tail_max_n.  GRID = false: one block with __syncthreads, for the small
+// levels at the bottom of the hierarchy, where grid barriers would dominate.
+// Every thread of every block runs the same control flow: decisions are taken
+// from grid reductions that every block finishes redundantly (same data, same
+// order, same result), and arena offsets are advanced identically by every
+// thread, so no extra barrier is needed to publish them.
+//
+// GB300 notes: FP64 issues at a small fraction of the FP32 rate, so counts,
+// scans, maxima and weight comparisons are integer work (bit patterns of
+// positive floats order like their values), and the FP64 sums the method
+// needs go through a shared halving tree instead of all-lane shuffles.
+// Data-dependent rounds (colouring, matching) walk atomic-append worklists, so
+// late rounds touch only live vertices and need one barrier and no reduction.
 #pragma once
 #include <cuda_runtime.h>
 #include <float.h>
@@ -55,35 +62,36 @@ FZD uint64_t gtime() {
 }
 
 // ---------------------------------------------------------------------------
-// Heavy-edge order K(e) = (w desc, h(min,max) asc, min asc, max asc); the hash
-// is only evaluated when weights tie exactly.
+// Heavy-edge order K(e) = (w desc, h(min,max) asc, min asc, max asc).  Weights
+// are positive, so their IEEE bit patterns order like their values: keys are
+// the float bits (fine level in float) or the double bits (FP64 levels).  The
+// hash is only evaluated when weights tie exactly.
 struct Best {
-  double w;
-  int v, lo, hi;
+  uint64_t wk;
   uint64_t h;
-  int hok;
+  int v, lo, hi, hok;
 };
 FZD void best_init(Best &b) {
   b.v = -1;
   b.hok = 0;
 }
-FZD bool best_beats(Best &b, double w, int u, int v, int tie) {
+FZD bool best_beats(Best &b, uint64_t wk, int u, int v, int tie) {
   if (b.v < 0) return true;
-  if (w != b.w) return w > b.w;
-  int lo = min(u, v), hi = max(u, v);
+  if (wk != b.wk) return wk > b.wk;
+  const int lo = min(u, v), hi = max(u, v);
   if (tie == 0) {
     if (!b.hok) {
       b.h = edge_hash(b.lo, b.hi);
       b.hok = 1;
     }
-    uint64_t h = edge_hash(lo, hi);
+    const uint64_t h = edge_hash(lo, hi);
     if (h != b.h) return h < b.h;
   }
   if (lo != b.lo) return lo < b.lo;
   return hi < b.hi;
 }
-FZD void best_set(Best &b, double w, int u, int v) {
-  b.w = w;
+FZD void best_set(Best &b, uint64_t wk, int u, int v) {
+  b.wk = wk;
   b.v = v;
   b.lo = min(u, v);
   b.hi = max(u, v);
@@ -91,40 +99,35 @@ FZD void best_set(Best &b, double w, int u, int v) {
 }
 
 // ---------------------------------------------------------------------------
-// reductions
-FZD void red_init(Red &r) {
-#pragma unroll
-  for (int k = 0; k < 6; k++) r.s[k] = 0.0;
-  r.mx = -DBL_MAX;
-  r.mxi = INT_MAX;
-  r.cnt = 0;
+// shared storage: a static __shared__ declared in a function is one allocation
+// per kernel
+constexpr int kShSort = 2048;  // u64 words of the raw buffer (16 KB)
+constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one thread
+
+FZD uint64_t *sh_raw() {
+  __shared__ uint64_t raw[kShSort];
+  return raw;
 }
-FZD void red_add(Red &a, const Red &b) {
-#pragma unroll
-  for (int k = 0; k < 6; k++) a.s[k] += b.s[k];
-  if (b.mx > a.mx || (b.mx == a.mx && b.mxi < a.mxi)) {
-    a.mx = b.mx;
-    a.mxi = b.mxi;
-  }
-  a.cnt += b.cnt;
+FZD int *sh_list() {
+  __shared__ int list[kCtaThreads];
+  return list;
 }
-FZD void red_shfl(Red &r, int off) {
-  Red o;
-#pragma unroll
-  for (int k = 0; k < 6; k++) o.s[k] = __shfl_xor_sync(0xffffffffu, r.s[k], off);
-  o.mx = __shfl_xor_sync(0xffffffffu, r.mx, off);
-  o.mxi = __shfl_xor_sync(0xffffffffu, r.mxi, off);
-  o.cnt = __shfl_xor_sync(0xffffffffu, r.cnt, off);
-  red_add(r, o);
+FZD int *sh_ints() {
+  __shared__ int v[8];
+  return v;
 }
-FZD void warp_red(Red &r) {
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) red_shfl(r, off);
+FZD long long *sh_ll() {
+  __shared__ long long v[3 * 33];
+  return v;
+}
+FZD double *sh_prof() {  // [2][PH_COUNT] totals, then [kMaxLevels][PH_COUNT] per level
+  __shared__ double v[2 * PH_COUNT + kMaxLevels * PH_COUNT];
+  return v;
 }
 
 // exclusive block scan of an int; *total = block sum.  All threads must call.
 FZD int block_scan(int v, int *total) {
-  __shared__ int ws[33];
+  __shared__ int wsum[33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int x = v;
 #pragma unroll
@@ -132,22 +135,94 @@ FZD int block_scan(int v, int *total) {
     int y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) ws[w] = x;
+  if (lane == 31) wsum[w] = x;
   __syncthreads();
   if (w == 0) {
-    int t = lane < nw ? ws[lane] : 0;
+    int t = lane < nw ? wsum[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       int y = __shfl_up_sync(0xffffffffu, t, o);
       if (lane >= o) t += y;
     }
-    ws[lane] = t;
+    wsum[lane] = t;
   }
   __syncthreads();
-  int incl = x + (w > 0 ? ws[w - 1] : 0);
-  *total = ws[nw - 1];
+  int incl = x + (w > 0 ? wsum[w - 1] : 0);
+  *total = wsum[nw - 1];
   __syncthreads();
   return incl - v;
+}
+
+// integer block reduction of (a sum, b sum, mx max); result in every thread
+FZD void block_ired(IRed &r) {
+  long long *s = sh_ll();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    r.a += __shfl_xor_sync(0xffffffffu, r.a, o);
+    r.b += __shfl_xor_sync(0xffffffffu, r.b, o);
+    r.mx = max(r.mx, __shfl_xor_sync(0xffffffffu, r.mx, o));
+  }
+  if (lane == 0) {
+    s[w] = r.a;
+    s[33 + w] = r.b;
+    s[66 + w] = r.mx;
+  }
+  __syncthreads();
+  if (w == 0) {
+    long long a = lane < nw ? s[lane] : 0, b = lane < nw ? s[33 + lane] : 0;
+    long long m = lane < nw ? s[66 + lane] : LLONG_MIN;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) {
+      s[32] = a;
+      s[65] = b;
+      s[98] = m;
+    }
+  }
+  __syncthreads();
+  r.a = s[32];
+  r.b = s[65];
+  r.mx = s[98];
+  __syncthreads();
+}
+
+// FP64 block sum of K <= 4 values by a shared halving tree (few FP64 adds),
+// then one warp; fixed order, result in every thread
+template <int K>
+FZD void block_dsum(double (&v)[K]) {
+  static_assert(K >= 1 && K <= 4, "block_dsum: K <= 4");
+  double *sh = reinterpret_cast<double *>(sh_raw());
+  const int t = threadIdx.x;
+  for (int s = blockDim.x >> 1; s >= 32; s >>= 1) {
+    if (t >= s && t < 2 * s) {
+#pragma unroll
+      for (int k = 0; k < K; k++) sh[k * s + (t - s)] = v[k];
+    }
+    __syncthreads();
+    if (t < s) {
+#pragma unroll
+      for (int k = 0; k < K; k++) v[k] += sh[k * s + t];
+    }
+    __syncthreads();
+  }
+  if (t < 32) {
+#pragma unroll
+    for (int k = 0; k < K; k++)
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (t == 0)
+#pragma unroll
+      for (int k = 0; k < K; k++) sh[k] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; k++) v[k] = sh[k];
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -202,23 +277,6 @@ FZD void block_bitonic(K *a, int len) {
   }
 }
 
-constexpr int kShSort = 2048;  // shared staging for block sorts (u64 keys)
-constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one thread
-
-// static __shared__ storage declared in a function is one allocation per kernel
-FZD uint64_t *sh_raw() {
-  __shared__ uint64_t raw[kShSort];
-  return raw;
-}
-FZD int *sh_list() {
-  __shared__ int list[kCtaThreads];
-  return list;
-}
-FZD int *sh_ints() {
-  __shared__ int v[8];
-  return v;
-}
-
 template <class K>
 FZD void block_sort(K *g, int len) {
   K *s = reinterpret_cast<K *>(sh_raw());
@@ -246,6 +304,9 @@ struct Eng {
   State *S;
   int tid, nthr, bid, nb, rb, kind;
   unsigned long long aoff, soff;
+  uint64_t t_last;  // lead thread only
+  unsigned ngen;    // grid barriers passed in this launch (same in every block)
+  int cur_level;    // level being worked on (profile)
   // control flow, identical in every thread
   int nlevels, setup_done, coarsest, coarsest_solved, solved, finalized;
 
@@ -266,10 +327,20 @@ struct Eng {
     coarsest_solved = S->coarsest_solved;
     solved = S->solved;
     finalized = S->finalized;
-    if (bid == 0 && threadIdx.x == 0) S->t_last = gtime();
+    t_last = 0;
+    ngen = 0;
+    cur_level = 0;
+    if (bid == 0) {
+      for (int i = threadIdx.x; i < 2 * PH_COUNT + kMaxLevels * PH_COUNT; i += blockDim.x) sh_prof()[i] = 0.0;
+      if (threadIdx.x == 0) t_last = gtime();
+    }
+    __syncthreads();
   }
   FZD bool lead() const { return bid == 0 && threadIdx.x == 0; }
-  FZD void fail(int code) { atomicCAS(&S->status, 0, code); }
+  FZD void fail(int code) {
+    atomicCAS(&S->failword, 0ull, ((unsigned long long)ngen << 32) | (unsigned)code);
+    atomicCAS(&S->status, 0, code);
+  }
   FZD int status() const { return *(volatile int *)&S->status; }
   FZD void persist() {
     if (lead()) {
@@ -280,6 +351,16 @@ struct Eng {
       S->solved = solved;
       S->finalized = finalized;
       if (status() == 0) S->arena_off = aoff;
+    }
+  }
+  FZD void flush_profile() {
+    if (lead()) {
+      for (int i = 0; i < PH_COUNT; i++) {
+        S->phase_ns[kind][i] += sh_prof()[i];
+        S->phase_bytes[kind][i] += sh_prof()[PH_COUNT + i];
+      }
+      for (int l = 0; l < kMaxLevels; l++)
+        for (int i = 0; i < PH_COUNT; i++) S->level_ns[l][i] += sh_prof()[2 * PH_COUNT + l * PH_COUNT + i];
     }
   }
 
@@ -304,51 +385,59 @@ struct Eng {
     return p;
   }
 
-  // barrier over every participating thread; false if the solve has failed
+  // Barrier over every participating thread; false if the solve has failed.
+  // Grid form: one atomic per block on a word whose top bit flips when the
+  // last block arrives (block 0 adds 2^31 - (nb - 1), the others add 1, so the
+  // low bits return to their start value), a bounded spin
+  // (barrier_timeout_ns), and a verdict every block agrees on: a failure
+  // counts at this barrier only if it was raised before it (failword carries
+  // the number of barriers the failing block had passed).
   FZD bool sync() {
     if (!GRID) return __syncthreads_and(status() == 0);
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-      volatile unsigned *genp = &S->bar_gen;
-      unsigned g = *genp;
+      const unsigned add = bid == 0 ? 0x80000000u - (unsigned)(nb - 1) : 1u;
       __threadfence();
-      unsigned arrived = atomicAdd(&S->bar_count, 1u);
-      if (arrived == (unsigned)nb - 1u) {
-        // every block has arrived, so every failure of the phase is visible:
-        // snapshot the verdict for all blocks before releasing them
-        atomicExch(&S->bar_count, 0u);
-        *(volatile int *)&S->bar_ok = status() == 0;
-        __threadfence();
-        atomicAdd(&S->bar_gen, 1u);
-      } else {
+      const unsigned old = atomicAdd(&S->bar_word, add);
+      bool done = (((old + add) ^ old) & 0x80000000u) != 0u;
+      if (!done) {
+        volatile unsigned *bw = &S->bar_word;
         const uint64_t t0 = gtime();
         const uint64_t lim = S->opt.barrier_timeout_ns;
         unsigned spins = 0;
-        while (*genp == g) {
-          if ((++spins & 255u) == 0u && gtime() - t0 > lim) {
-            fail(ST_ETIMEOUT);
-            break;
-          }
-          __nanosleep(64);
+        while (!done) {
+          done = ((*bw ^ old) & 0x80000000u) != 0u;
+          if (!done && (++spins & 255u) == 0u && gtime() - t0 > lim) break;
         }
       }
       __threadfence();
-      s_ok = (*genp != g) ? *(volatile int *)&S->bar_ok : 0;
+      if (!done) {
+        fail(ST_ETIMEOUT);
+        s_ok = 0;
+      } else {
+        const unsigned long long fw = *(volatile unsigned long long *)&S->failword;
+        s_ok = fw == 0ull || (unsigned)(fw >> 32) > ngen;
+      }
     }
     __syncthreads();
+    ngen++;
     return s_ok != 0;
   }
 
-  // profile: attribute the time since the last mark to phase ph
+  // profile: attribute the time since the last mark to phase ph (lead only)
   FZD void mark(int ph, double bytes) {
-    if (lead()) {
-      uint64_t t = gtime();
-      S->phase_ns[kind][ph] += (double)(t - S->t_last);
-      S->phase_bytes[kind][ph] += bytes;
-      S->t_last = t;
-    }
+    const uint64_t t = gtime();
+    const double dt = (double)(t - t_last);
+    sh_prof()[ph] += dt;
+    sh_prof()[PH_COUNT + ph] += bytes;
+    sh_prof()[2 * PH_COUNT + cur_level * PH_COUNT + ph] += dt;
+    t_last = t;
   }
+#define FZ_MARK(ph, bytes)           \
+  do {                               \
+    if (lead()) mark((ph), (bytes)); \
+  } while (0)
 
   FZD void chunk(long long n, int &lo, int &hi) const {
     long long ch = (n + nb - 1) / nb;
@@ -360,81 +449,113 @@ struct Eng {
     hi = (int)b;
   }
 
-  // Grid-wide reduction of per-thread partials.  On return r holds the total
-  // in every thread; *pre_cnt / *pre_s0 receive the sums of cnt / s[0] over
-  // the blocks before this one (for chunked scans).
-  FZD bool grid_reduce(Red &r, long long *pre_cnt = nullptr, double *pre_s0 = nullptr) {
-    __shared__ Red s_w[32];
-    __shared__ Red s_tot;
-    __shared__ long long s_pc;
-    __shared__ double s_ps;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    warp_red(r);
-    if (lane == 0) s_w[w] = r;
-    __syncthreads();
-    Red *part = S->part + rb * kMaxBlocks;
-    if (w == 0) {
-      Red a;
-      red_init(a);
-      if (lane < nw) a = s_w[lane];
-      warp_red(a);
-      if (lane == 0) {
-        if (GRID) part[bid] = a;
-        else s_tot = a;
-      }
-    }
+  // Integer grid reduction: sums a, b and maximum mx; pre_a / pre_b receive
+  // the sums over the blocks before this one (chunked scans).
+  FZD bool grid_ired(IRed &r, long long *pre_a = nullptr, long long *pre_b = nullptr) {
+    block_ired(r);
+    long long pa = 0, pb = 0;
     if (GRID) {
+      IRed *part = S->ipart + rb * kMaxBlocks;
+      if (threadIdx.x == 0) part[bid] = r;
       if (!sync()) return false;
-      if (w == 0) {
-        Red a;
-        red_init(a);
-        long long pc = 0;
-        double ps = 0.0;
-        for (int b = lane; b < nb; b += 32) {
-          Red p = part[b];
-          if (b < bid) {
-            pc += p.cnt;
-            ps += p.s[0];
+      long long *s = sh_ll();
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        long long a = 0, b = 0, m = LLONG_MIN, qa = 0, qb = 0;
+        for (int k = lane; k < nb; k += 32) {
+          const IRed p = part[k];
+          a += p.a;
+          b += p.b;
+          m = max(m, p.mx);
+          if (k < bid) {
+            qa += p.a;
+            qb += p.b;
           }
-          red_add(a, p);
         }
-        warp_red(a);
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-          pc += __shfl_xor_sync(0xffffffffu, pc, off);
-          ps += __shfl_xor_sync(0xffffffffu, ps, off);
+        for (int o = 16; o >= 1; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+          qa += __shfl_xor_sync(0xffffffffu, qa, o);
+          qb += __shfl_xor_sync(0xffffffffu, qb, o);
         }
         if (lane == 0) {
-          s_tot = a;
-          s_pc = pc;
-          s_ps = ps;
+          s[0] = a;
+          s[1] = b;
+          s[2] = m;
+          s[3] = qa;
+          s[4] = qb;
         }
       }
+      __syncthreads();
+      r.a = s[0];
+      r.b = s[1];
+      r.mx = s[2];
+      pa = s[3];
+      pb = s[4];
+      __syncthreads();
+      rb ^= 1;
     } else {
-      if (threadIdx.x == 0) {
-        s_pc = 0;
-        s_ps = 0.0;
-      }
       if (!__syncthreads_and(status() == 0)) return false;
     }
-    __syncthreads();
-    r = s_tot;
-    if (pre_cnt) *pre_cnt = s_pc;
-    if (pre_s0) *pre_s0 = s_ps;
-    __syncthreads();
-    rb ^= 1;
+    if (pre_a) *pre_a = pa;
+    if (pre_b) *pre_b = pb;
     return true;
   }
 
-  // setup weights: FP64 on coarse levels, the caller's float or double on the fine level
+  // FP64 grid sum of K <= 4 values (deterministic order)
+  template <int K>
+  FZD bool grid_dsum(double (&v)[K]) {
+    block_dsum<K>(v);
+    if (GRID) {
+      double *part = S->dpart + (size_t)rb * kMaxBlocks * kDSum;
+      if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) part[bid * kDSum + k] = v[k];
+      if (!sync()) return false;
+      double *sh = reinterpret_cast<double *>(sh_raw());
+      if (threadIdx.x < 32) {
+        double a[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) a[k] = 0.0;
+        for (int b = threadIdx.x; b < nb; b += 32)
+#pragma unroll
+          for (int k = 0; k < K; k++) a[k] += part[b * kDSum + k];
+#pragma unroll
+        for (int k = 0; k < K; k++)
+#pragma unroll
+          for (int o = 16; o >= 1; o >>= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
+        if (threadIdx.x == 0)
+#pragma unroll
+          for (int k = 0; k < K; k++) sh[k] = a[k];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < K; k++) v[k] = sh[k];
+      __syncthreads();
+      rb ^= 1;
+    } else {
+      if (!__syncthreads_and(status() == 0)) return false;
+    }
+    return true;
+  }
+
+  // setup weights: FP64 on coarse levels, the caller's float or double on the
+  // fine level; key() gives the order-preserving bit pattern for comparisons
   struct W {
     const double *w64;
     const float *w32;
     FZD double operator[](int e) const { return w64 ? w64[e] : (double)w32[e]; }
+    FZD uint64_t key(int e) const {
+      return w64 ? (uint64_t)__double_as_longlong(w64[e]) : (uint64_t)__float_as_uint(w32[e]);
+    }
   };
   FZD static W wof(const Level *L) { return W{L->w64, L->w32}; }
 
   FZD bool elig(int n) const { return GRID ? (n > S->opt.tail_max_n) : (n <= S->opt.tail_max_n); }
+
+  FZD int wl_read(int slot) const { return *(volatile int *)&S->wl_cnt[slot]; }
 
   // ---- A1: ingest the fine level (Def 2.1) ---------------------------------
   FZD bool ingest() {
@@ -446,8 +567,9 @@ struct Eng {
     const int validate = S->opt.validate;
     if (validate) {
       for (int i = tid; i <= n; i += nthr) {
-        int a = rp[i];
-        bool bad = a < 0 || a > nnz || (i == 0 && a != 0) || (i == n && a != nnz) || (i < n && rp[i + 1] < a);
+        const int a = rp[i];
+        const bool bad =
+            a < 0 || a > nnz || (i == 0 && a != 0) || (i == n && a != nnz) || (i < n && rp[i + 1] < a);
         if (bad) {
           atomicMin((unsigned long long *)&S->bad_index, (unsigned long long)i);
           fail(ST_EINVAL);
@@ -459,8 +581,7 @@ struct Eng {
     if (!d) return false;
     int lo, hi;
     chunk(n, lo, hi);
-    Red r;
-    red_init(r);
+    IRed r{0, 0, 0};
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       const int e0 = rp[i], e1 = rp[i + 1];
       double di = 0.0;
@@ -473,7 +594,7 @@ struct Eng {
           if (!bad && j != i) {
             int a = rp[j], b = rp[j + 1] - 1, f = -1;
             while (a <= b) {
-              int m = (a + b) >> 1, cm = ci[m];
+              const int m = (a + b) >> 1, cm = ci[m];
               if (cm == i) {
                 f = m;
                 break;
@@ -481,7 +602,7 @@ struct Eng {
               if (cm < i) a = m + 1;
               else b = m - 1;
             }
-            bad = f < 0 || (wf64 ? wd[f] : (double)wf[f]) != w;
+            bad = f < 0 || (wf64 ? wd[f] != wd[e] : wf[f] != wf[e]);
           }
           if (bad) {
             atomicMin((unsigned long long *)&S->bad_index, (unsigned long long)e);
@@ -496,18 +617,18 @@ struct Eng {
         di += w;
       }
       d[i] = di;
-      r.cnt += e1 - e0 - loops;
-      r.s[0] += (double)loops;
-      r.mx = fmax(r.mx, di);
+      r.a += e1 - e0 - loops;
+      r.b += loops;
+      r.mx = max(r.mx, (long long)__double_as_longlong(di));  // d >= 0: bit order = value order
     }
     long long pre = 0;
-    if (!grid_reduce(r, &pre)) return false;
-    const long long m = r.cnt;
-    const double maxd = r.mx;
+    if (!grid_ired(r, &pre)) return false;
+    const long long m = r.a;
+    const double maxd = __longlong_as_double(r.mx);
     int *rowptr = (int *)rp, *col = (int *)ci;
     double *w64 = wf64 ? (double *)wd : nullptr;
     float *w32 = wf64 ? nullptr : (float *)wf;
-    if (r.s[0] > 0.0) {  // drop self-loops
+    if (r.b > 0) {  // drop self-loops
       rowptr = (int *)aalloc(4ull * (n + 1));
       col = (int *)aalloc(4ull * (m > 0 ? m : 1));
       void *wn = aalloc((wf64 ? 8ull : 4ull) * (m > 0 ? m : 1));
@@ -516,12 +637,12 @@ struct Eng {
       w32 = wf64 ? nullptr : (float *)wn;
       long long run = pre;
       for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
-        int i = t0 + threadIdx.x;
+        const int i = t0 + threadIdx.x;
         int kept = 0;
         if (i < hi)
           for (int e = rp[i]; e < rp[i + 1]; e++) kept += ci[e] != i;
         int tot;
-        int ex = block_scan(kept, &tot);
+        const int ex = block_scan(kept, &tot);
         if (i < hi) {
           int o = (int)(run + ex);
           rowptr[i] = o;
@@ -535,8 +656,7 @@ struct Eng {
         }
         run += tot;
       }
-      if (hi == n && lo < hi) rowptr[n] = (int)m;
-      if (n > 0 && lo == hi && bid == nb - 1) rowptr[n] = (int)m;
+      if (lead()) rowptr[n] = (int)m;
     }
     if (lead()) {
       Level &L = S->lv[0];
@@ -550,27 +670,52 @@ struct Eng {
       L.sigma = 2.0 * maxd;
     }
     if (!sync()) return false;
-    mark(PH_INGEST, 12.0 * n + (4.0 + (wf64 ? 8.0 : 4.0)) * nnz * (validate ? 2.0 : 1.0));
+    FZ_MARK(PH_INGEST, 12.0 * n + (4.0 + (wf64 ? 8.0 : 4.0)) * nnz * (validate ? 2.0 : 1.0));
     return true;
   }
 
   // ---- A6: Jones-Plassmann colouring, priority (h(v), v) --------------------
+  // Each block owns the vertices of its chunk and keeps its own worklists
+  // (three rotating lists inside the chunk's range, counters in shared
+  // memory).  Round r reads list r%3 (the whole chunk in round 0) and appends
+  // the vertices still uncoloured to list (r+1)%3; one global atomic per block
+  // per round sums the survivors for the termination test, and the global
+  // counter of list (r+2)%3 is cleared meanwhile (nobody uses it in round r).
   FZD bool colour(int l) {
+    cur_level = l;
     Level *L = &S->lv[l];
     const int n = L->n;
     const int *rp = L->rowptr, *ci = L->col;
     soff = 0;
     int *cround = (int *)salloc(4ull * n);
+    int *list[3];
+    for (int k = 0; k < 3; k++) list[k] = (int *)salloc(4ull * n);
     int *color = (int *)aalloc(4ull * n);
-    if (!cround || !color) return false;
+    if (!cround || !list[0] || !list[1] || !list[2] || !color) return false;
+    int lo, hi;
+    chunk(n, lo, hi);
+    int *s_cnt = sh_ints();  // [0..2] block list counters, [3] block colour max
     for (int v = tid; v < n; v += nthr) cround[v] = INT_MAX;
+    if (threadIdx.x == 0) {
+      s_cnt[0] = hi - lo;
+      s_cnt[1] = 0;
+      s_cnt[2] = 0;
+      s_cnt[3] = -1;
+    }
+    if (lead()) {
+      S->wl_cnt[1] = 0;
+      S->wl_cnt[2] = 0;
+      S->col_max = -1;
+    }
     if (!sync()) return false;
-    int maxc = -1, r = 0;
+    int r = 0;
+    long long visits = 0;
     for (;; r++) {
-      Red red;
-      red_init(red);
-      for (int v = tid; v < n; v += nthr) {
-        if (cround[v] != INT_MAX) continue;
+      const int cur = r % 3, nxt = (r + 1) % 3, clr = (r + 2) % 3;
+      if (lead() && r > 0) S->wl_cnt[clr] = 0;
+      const int cnt = s_cnt[cur];
+      for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int v = r == 0 ? lo + q : list[cur][lo + q];
         const uint64_t hv = vtx_hash(v);
         bool top = true;
         const int e0 = rp[v], e1 = rp[v + 1];
@@ -585,7 +730,7 @@ struct Eng {
           }
         }
         if (!top) {
-          red.cnt++;
+          list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
           continue;
         }
         int base = 0, c = 0;
@@ -606,13 +751,20 @@ struct Eng {
         }
         color[v] = c;
         cround[v] = r;
-        red.mx = fmax(red.mx, (double)c);
+        atomicMax(&s_cnt[3], c);
       }
-      if (!grid_reduce(red)) return false;
-      if (red.mx >= 0.0) maxc = max(maxc, (int)red.mx);
-      if (red.cnt == 0) break;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        if (s_cnt[nxt]) atomicAdd(&S->wl_cnt[nxt], s_cnt[nxt]);
+        s_cnt[cur] = 0;  // becomes the append target of round r + 2
+      }
+      visits += cnt;
+      if (!sync()) return false;
+      if (wl_read(nxt) == 0) break;
     }
-    const int ncol = maxc + 1;
+    if (threadIdx.x == 0 && s_cnt[3] >= 0) atomicMax(&S->col_max, s_cnt[3]);
+    if (!sync()) return false;
+    const int ncol = *(volatile int *)&S->col_max + 1;
     if (ncol > kMaxColors) {
       fail(ST_ENOTSUP);
       return false;
@@ -623,12 +775,13 @@ struct Eng {
       L->color_rounds = r + 1;
     }
     if (!sync()) return false;
-    mark(PH_COLOR, (double)(r + 1) * (8.0 * n + 8.0 * L->nnz));
+    FZ_MARK(PH_COLOR, 8.0 * n + (double)visits * 12.0 * nb + 4.0 * L->nnz);
     return true;
   }
 
   // ---- colour-order copy of the level for the solve phase -------------------
   FZD bool reorder(int l) {
+    cur_level = l;
     Level *L = &S->lv[l];
     const int n = L->n, nnz = L->nnz, C = L->ncolors;
     const int *rp = L->rowptr, *ci = L->col, *color = L->color;
@@ -643,8 +796,8 @@ struct Eng {
     T *y = (T *)aalloc(sizeof(T) * (unsigned long long)n);
     int *sagg = (int *)aalloc(4ull * n);
     if (!hist || !perm || !iperm || !colstart || !srp || !scol || !sw || !x || !y || !sagg) return false;
-    int *sh_cnt = reinterpret_cast<int *>(sh_raw());  // [kMaxColors]
-    int *sh_base = sh_cnt + kMaxColors;              // [kMaxColors]
+    int *sh_cnt = reinterpret_cast<int *>(sh_raw());                     // [kMaxColors]
+    int *sh_base = sh_cnt + kMaxColors;                                 // [kMaxColors]
     int(*wc)[64] = reinterpret_cast<int(*)[64]>(sh_base + kMaxColors);  // [32][64], C <= 64 only
     int lo, hi;
     chunk(n, lo, hi);
@@ -657,7 +810,7 @@ struct Eng {
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
       int t = 0, p = 0;
       for (int b = 0; b < nb; b++) {
-        int h = hist[(size_t)c * nb + b];
+        const int h = hist[(size_t)c * nb + b];
         t += h;
         if (b < bid) p += h;
       }
@@ -690,7 +843,7 @@ struct Eng {
           const int c = threadIdx.x;
           int acc = sh_base[c];
           for (int ww = 0; ww < nw; ww++) {
-            int t = wc[ww][c];
+            const int t = wc[ww][c];
             wc[ww][c] = acc;
             acc += t;
           }
@@ -711,7 +864,7 @@ struct Eng {
         for (int c = 0; c < C; c++) {
           if (!__syncthreads_or(cv == c)) continue;
           int tot;
-          int ex = block_scan(cv == c, &tot);
+          const int ex = block_scan(cv == c, &tot);
           if (cv == c) {
             const int pos = sh_base[c] + ex;
             perm[pos] = v;
@@ -725,14 +878,13 @@ struct Eng {
     }
     if (!sync()) return false;
     // row pointers of the colour-order copy
-    Red red;
-    red_init(red);
+    IRed red{0, 0, 0};
     for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
       const int v = perm[k];
-      red.cnt += rp[v + 1] - rp[v];
+      red.a += rp[v + 1] - rp[v];
     }
     long long pre = 0;
-    if (!grid_reduce(red, &pre)) return false;
+    if (!grid_ired(red, &pre)) return false;
     long long run = pre;
     const W wl = wof(L);
     for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
@@ -772,12 +924,19 @@ struct Eng {
       L->sagg = sagg;
     }
     if (!sync()) return false;
-    mark(PH_REORDER, 28.0 * n + (8.0 + (L->w64 ? 8.0 : 4.0) + 4.0 + sizeof(T)) * nnz);
+    FZ_MARK(PH_REORDER, 28.0 * n + (8.0 + (L->w64 ? 8.0 : 4.0) + 4.0 + sizeof(T)) * nnz);
     return true;
   }
 
   // ---- A2: heavy-edge matching by handshake rounds ---------------------------
+  // Phases alternate pick / match over block-owned worklists (as in colour()):
+  //   pick:  an active vertex points at its best unmatched neighbour under K;
+  //          vertices with a candidate go to the next list, the others have no
+  //          free neighbour now or later and drop out;
+  //   match: mutual candidates become pairs; the rest are active again.
+  // Stop after a pick that found no candidate, or a match that left nobody.
   FZD bool match(int l) {
+    cur_level = l;
     Level *L = &S->lv[l];
     const int n = L->n;
     const int *rp = L->rowptr, *ci = L->col;
@@ -785,47 +944,80 @@ struct Eng {
     const W wl = wof(L);
     int *mate = (int *)aalloc(4ull * n);
     int *cand = (int *)salloc(4ull * n);
-    if (!mate || !cand) return false;
-    int r = 0;
-    double bytes = 0.0;
-    for (;; r++) {
-      Red red;
-      red_init(red);
-      for (int v = tid; v < n; v += nthr) {
-        if (r == 0) mate[v] = -1;
-        else if (mate[v] >= 0 || cand[v] == -2) continue;
-        Best b;
-        best_init(b);
-        for (int e = rp[v]; e < rp[v + 1]; e++) {
-          const int u = ci[e];
-          if (r > 0 && mate[u] >= 0) continue;
-          const double wv = wl[e];
-          if (best_beats(b, wv, v, u, tie)) best_set(b, wv, v, u);
+    int *list[3];
+    for (int k = 0; k < 3; k++) list[k] = (int *)salloc(4ull * n);
+    if (!mate || !cand || !list[0] || !list[1] || !list[2]) return false;
+    int lo, hi;
+    chunk(n, lo, hi);
+    int *s_cnt = sh_ints();
+    if (threadIdx.x == 0) {
+      s_cnt[0] = hi - lo;
+      s_cnt[1] = 0;
+      s_cnt[2] = 0;
+    }
+    if (lead()) {
+      S->wl_cnt[1] = 0;
+      S->wl_cnt[2] = 0;
+    }
+    for (int v = tid; v < n; v += nthr) mate[v] = -1;
+    if (!sync()) return false;
+    int rounds = 0;
+    long long visits = 0;
+    for (int ph = 0;; ph++) {
+      const int cur = ph % 3, nxt = (ph + 1) % 3, clr = (ph + 2) % 3;
+      if (lead() && ph > 0) S->wl_cnt[clr] = 0;
+      const int cnt = s_cnt[cur];
+      if ((ph & 1) == 0) {  // pick
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+          const int v = ph == 0 ? lo + q : list[cur][lo + q];
+          Best b;
+          best_init(b);
+          for (int e = rp[v]; e < rp[v + 1]; e++) {
+            const int u = ci[e];
+            if (ph > 0 && mate[u] >= 0) continue;
+            const uint64_t wk = wl.key(e);
+            if (best_beats(b, wk, v, u, tie)) best_set(b, wk, v, u);
+          }
+          if (b.v >= 0) {
+            cand[v] = b.v;
+            list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
+          }
         }
-        cand[v] = b.v >= 0 ? b.v : -2;
-        red.cnt += b.v >= 0;
-        red.s[0] += (double)(rp[v + 1] - rp[v]);
+      } else {  // match
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+          const int v = list[cur][lo + q];
+          const int c = cand[v];
+          if (cand[c] == v) mate[v] = c;
+          else list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
+        }
       }
-      if (!grid_reduce(red)) return false;
-      bytes += 12.0 * n + red.s[0] * (8.0 + (L->w64 ? 8.0 : 4.0));
-      if (red.cnt == 0) break;
-      for (int v = tid; v < n; v += nthr) {
-        const int c = cand[v];
-        if (c >= 0 && cand[c] == v) mate[v] = c;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        if (s_cnt[nxt]) atomicAdd(&S->wl_cnt[nxt], s_cnt[nxt]);
+        s_cnt[cur] = 0;
       }
+      visits += cnt;
       if (!sync()) return false;
+      const int total = wl_read(nxt);
+      if ((ph & 1) == 0) {
+        if (total == 0) break;
+        rounds++;
+      } else if (total == 0) {
+        break;
+      }
     }
     if (lead()) {
       L->mate = mate;
-      L->match_rounds = r;
+      L->match_rounds = rounds;
     }
     if (!sync()) return false;
-    mark(PH_MATCH, bytes);
+    FZ_MARK(PH_MATCH, 4.0 * n + (double)visits * nb * (8.0 + 4.0 * 4 + (L->w64 ? 8.0 : 4.0) * 4));
     return true;
   }
 
   // ---- A3: aggregates from the matching; returns nc (or -1: stop coarsening)
   FZD bool aggregate(int l, int &nc_out, GalerkinScratch &G) {
+    cur_level = l;
     Level *L = &S->lv[l];
     const int n = L->n;
     const int *rp = L->rowptr, *ci = L->col, *mate = L->mate;
@@ -834,15 +1026,14 @@ struct Eng {
     const double stall = S->opt.stall_ratio;
     int lo, hi;
     chunk(n, lo, hi);
-    Red red;
-    red_init(red);
+    IRed red{0, 0, 0};
     for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
       const int m = mate[v];
-      red.cnt += (m >= 0) ? (v < m) : (rp[v + 1] == rp[v]);
+      red.a += (m >= 0) ? (v < m) : (rp[v + 1] == rp[v]);
     }
     long long pre = 0;
-    if (!grid_reduce(red, &pre)) return false;
-    const long long nc = red.cnt;
+    if (!grid_ired(red, &pre)) return false;
+    const long long nc = red.a;
     nc_out = -1;
     if (nc < 2 || (double)nc > stall * (double)n) return true;
     int *agg = (int *)aalloc(4ull * n);
@@ -890,8 +1081,8 @@ struct Eng {
         best_init(b);
         for (int e = rp[v]; e < rp[v + 1]; e++) {
           const int u = ci[e];
-          const double wv = wl[e];
-          if (best_beats(b, wv, v, u, tie)) best_set(b, wv, v, u);
+          const uint64_t wk = wl.key(e);
+          if (best_beats(b, wk, v, u, tie)) best_set(b, wk, v, u);
         }
         const int u = b.v, mu = mate[u];
         if (mu < 0) {  // matching not maximal: cannot happen
@@ -909,13 +1100,14 @@ struct Eng {
       L->nc = (int)nc;
     }
     if (!sync()) return false;
-    mark(PH_AGG, 24.0 * n + 12.0 * L->nnz);
+    FZ_MARK(PH_AGG, 24.0 * n + 12.0 * L->nnz);
     nc_out = (int)nc;
     return true;
   }
 
   // ---- A4: Galerkin coarse operator I L I^T ---------------------------------
   FZD bool galerkin(int l, int nc, GalerkinScratch &G) {
+    cur_level = l;
     Level *L = &S->lv[l];
     const int n = L->n;
     const int *rp = L->rowptr, *ci = L->col;
@@ -933,18 +1125,16 @@ struct Eng {
     // G2: member and segment pointers (chunked scans over aggregates)
     int lo, hi;
     chunk(nc, lo, hi);
-    Red red;
-    red_init(red);
+    IRed red{0, 0, 0};
     for (int I = lo + threadIdx.x; I < hi; I += blockDim.x) {
-      red.cnt += G.cnt[I];
-      red.s[0] += (double)G.tcnt[I];
+      red.a += G.cnt[I];
+      red.b += G.tcnt[I];
     }
-    long long preA = 0;
-    double preB = 0.0;
-    if (!grid_reduce(red, &preA, &preB)) return false;
-    const long long ttot = (long long)red.s[0];
+    long long preA = 0, preB = 0;
+    if (!grid_ired(red, &preA, &preB)) return false;
+    const long long ttot = red.b;
     {
-      long long ra = preA, rbb = (long long)preB;
+      long long ra = preA, rbb = preB;
       for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
         const int I = t0 + threadIdx.x;
         const int a = I < hi ? G.cnt[I] : 0, b = I < hi ? G.tcnt[I] : 0;
@@ -1032,7 +1222,7 @@ struct Eng {
     }
     if (!sync()) return false;
     // G6: sort each segment by (J, slot); distinct J per coarse row
-    red_init(red);
+    red = IRed{0, 0, 0};
     {
       int *s_big = sh_list();
       int &s_nbig = sh_ints()[0];
@@ -1049,7 +1239,7 @@ struct Eng {
             for (int k = 0; k < len; k++)
               dcount += (k == 0) || ((G.keys[s + k] >> 32) != (G.keys[s + k - 1] >> 32));
             G.dcnt[I] = dcount;
-            red.cnt += dcount;
+            red.a += dcount;
           } else {
             s_big[atomicAdd(&s_nbig, 1)] = I;
           }
@@ -1069,22 +1259,22 @@ struct Eng {
           __syncthreads();
           if (threadIdx.x == 0) {
             G.dcnt[Ib] = s_dist;
-            red.cnt += s_dist;
+            red.a += s_dist;
           }
           __syncthreads();
         }
       }
     }
     long long pre = 0;
-    if (!grid_reduce(red, &pre)) return false;
-    const long long nnzc = red.cnt;
+    if (!grid_ired(red, &pre)) return false;
+    const long long nnzc = red.a;
     int *crp = (int *)aalloc(4ull * (nc + 1));
     int *ccol = (int *)aalloc(4ull * (nnzc > 0 ? nnzc : 1));
     double *cw = (double *)aalloc(8ull * (nnzc > 0 ? nnzc : 1));
     double *cd = (double *)aalloc(8ull * nc);
     if (!crp || !ccol || !cw || !cd) return false;
     // G7: coarse row pointers, then the summed weights in (J, slot) order
-    red_init(red);
+    red = IRed{0, 0, 0};
     {
       long long run = pre;
       int *s_big = sh_list();
@@ -1117,7 +1307,7 @@ struct Eng {
             }
             for (int q = crp[I]; q < p; q++) dI += cw[q];
             cd[I] = dI;
-            red.mx = fmax(red.mx, dI);
+            red.mx = max(red.mx, (long long)__double_as_longlong(dI));
           } else {
             s_big[atomicAdd(&s_nbig, 1)] = I;
           }
@@ -1149,14 +1339,14 @@ struct Eng {
             double dI = 0.0;
             for (int q2 = p0; q2 < p0 + gr; q2++) dI += cw[q2];
             cd[Ib] = dI;
-            red.mx = fmax(red.mx, dI);
+            red.mx = max(red.mx, (long long)__double_as_longlong(dI));
           }
           __syncthreads();
         }
       }
       if (lead()) crp[nc] = (int)nnzc;
     }
-    if (!grid_reduce(red)) return false;
+    if (!grid_ired(red)) return false;
     if (lead()) {
       Level &C = S->lv[l + 1];
       C.n = nc;
@@ -1166,18 +1356,19 @@ struct Eng {
       C.w64 = cw;
       C.w32 = nullptr;
       C.d = cd;
-      C.sigma = 2.0 * red.mx;
+      C.sigma = 2.0 * __longlong_as_double(red.mx);
       C.agg = nullptr;
       C.mate = nullptr;
       C.nc = 0;
     }
     if (!sync()) return false;
-    mark(PH_GALERKIN, 40.0 * n + (12.0 + 8.0 + 16.0 * 3.0) * L->nnz);
+    FZ_MARK(PH_GALERKIN, 40.0 * n + (12.0 + 8.0 + 16.0 * 3.0) * L->nnz);
     return true;
   }
 
   // ---- A7: coarsest level: connectivity, random start ---------------------
   FZD bool coarsest_solve(int J) {
+    cur_level = J;
     Level *L = &S->lv[J];
     const int n = L->n;
     const int *rp = L->rowptr, *ci = L->col, *iperm = L->iperm;
@@ -1187,56 +1378,54 @@ struct Eng {
     for (int v = tid; v < n; v += nthr) lab[v] = v;
     if (!sync()) return false;
     for (int it = 0;; it++) {
-      Red red;
-      red_init(red);
+      IRed red{0, 0, 0};
       for (int v = tid; v < n; v += nthr) {
         int m = lab[v];
         for (int e = rp[v]; e < rp[v + 1]; e++) m = min(m, lab[ci[e]]);
         if (m < lab[v]) {
           lab[v] = m;
-          red.cnt++;
+          red.a++;
         }
       }
-      if (!grid_reduce(red)) return false;
-      if (red.cnt == 0) break;
+      if (!grid_ired(red)) return false;
+      if (red.a == 0) break;
       if (it > n) {
         fail(ST_EINVAL);
         return false;
       }
     }
     {
-      Red red;
-      red_init(red);
-      for (int v = tid; v < n; v += nthr) red.cnt += lab[v] != 0;
-      if (!grid_reduce(red)) return false;
-      if (red.cnt != 0) {
+      IRed red{0, 0, 0};
+      for (int v = tid; v < n; v += nthr) red.a += lab[v] != 0;
+      if (!grid_ired(red)) return false;
+      if (red.a != 0) {
         fail(ST_EDISC);
         return false;
       }
     }
     T *x = (T *)L->x;
-    Red red;
-    red_init(red);
+    double acc[2] = {0.0, 0.0};
     const uint64_t seed = S->opt.seed;
     for (int i = tid; i < n; i += nthr) {
       const T v = (T)uniform01(seed, (uint64_t)i);
       x[iperm[i]] = v;
-      red.s[0] += (double)v;
-      red.s[1] += (double)v * (double)v;
+      acc[0] += (double)v;
+      acc[1] += (double)v * (double)v;
     }
-    if (!grid_reduce(red)) return false;
-    const double mu = red.s[0] / n, var = red.s[1] - red.s[0] * mu;
+    if (!grid_dsum<2>(acc)) return false;
+    const double mu = acc[0] / n, var = acc[1] - acc[0] * mu;
     const double g = S->opt.guard;
     if (!(var > g * g)) {
       fail(ST_EDEGEN);
       return false;
     }
-    mark(PH_COARSEST, 16.0 * n + 8.0 * L->nnz);
+    FZ_MARK(PH_COARSEST, 16.0 * n + 8.0 * L->nnz);
     return smooth(J, S->opt.pi_max_iters_coarsest, mu, 1.0 / sqrt(var), PH_COARSEST);
   }
 
   // ---- A8: prolongation y^j = I^T y^{j+1} ----------------------------------
   FZD bool prolong(int l) {
+    cur_level = l;
     Level *F = &S->lv[l];
     const Level *Cl = &S->lv[l + 1];
     const int n = F->n;
@@ -1244,22 +1433,21 @@ struct Eng {
     const T muc = (T)Cl->mu, sc = (T)Cl->s;
     T *x = (T *)F->x;
     const int *sagg = F->sagg;
-    Red red;
-    red_init(red);
+    double acc[2] = {0.0, 0.0};
     for (int k = tid; k < n; k += nthr) {
       const T v = (xc[sagg[k]] - muc) * sc;
       x[k] = v;
-      red.s[0] += (double)v;
-      red.s[1] += (double)v * (double)v;
+      acc[0] += (double)v;
+      acc[1] += (double)v * (double)v;
     }
-    if (!grid_reduce(red)) return false;
-    const double mu = red.s[0] / n, var = red.s[1] - red.s[0] * mu;
+    if (!grid_dsum<2>(acc)) return false;
+    const double mu = acc[0] / n, var = acc[1] - acc[0] * mu;
     const double g = S->opt.guard;
     if (!(var > g * g)) {
       fail(ST_EDEGEN);
       return false;
     }
-    mark(PH_PROLONG, (4.0 + 2.0 * sizeof(T)) * n);
+    FZ_MARK(PH_PROLONG, (4.0 + 2.0 * sizeof(T)) * n);
     return smooth(l, S->opt.pi_max_iters, mu, 1.0 / sqrt(var), PH_GS);
   }
 
@@ -1271,34 +1459,36 @@ struct Eng {
     const T *sw = (const T *)L->sw;
     T *A = (T *)L->x, *B = (T *)L->y;
     const double g = S->opt.guard;
+    const int nsweeps = S->opt.gs_sweeps;
     const double sweep_bytes = 4.0 * (n + 1) + (4.0 + sizeof(T)) * nnz + 2.0 * sizeof(T) * n;
+    const int ph_gs = gs_phase == PH_COARSEST ? PH_COARSEST : PH_GS;
+    const int ph_pi = gs_phase == PH_COARSEST ? PH_COARSEST : PH_PI;
     int sweeps = 0;
-    for (int k = 0; k < S->opt.gs_sweeps; k++) {
-      Red red;
-      red_init(red);
+    for (int k = 0; k < nsweeps; k++) {
+      double acc[2] = {0.0, 0.0};
       const T muT = (T)mu, sT = (T)s;
       for (int c = 0; c < C; c++) {
         const int cs = cst[c], ce = cst[c + 1];
         for (int i = cs + tid; i < ce; i += nthr) {
-          T acc = (T)0, dsum = (T)0;
+          T num = (T)0, dsum = (T)0;
           const int e1 = srp[i + 1];
           for (int e = srp[i]; e < e1; e++) {
             const int j = scol[e];
             const T wv = sw[e];
             const T xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
-            acc += wv * xj;
+            num += wv * xj;
             dsum += wv;
           }
-          const T xi = acc / dsum;
+          const T xi = num / dsum;
           B[i] = xi;
-          red.s[0] += (double)xi;
-          red.s[1] += (double)xi * (double)xi;
+          acc[0] += (double)xi;
+          acc[1] += (double)xi * (double)xi;
         }
         if (c + 1 < C && !sync()) return false;
       }
-      if (!grid_reduce(red)) return false;
-      mark(gs_phase == PH_COARSEST ? PH_COARSEST : PH_GS, sweep_bytes);
-      const double m2 = red.s[0] / n, var = red.s[1] - red.s[0] * m2;
+      if (!grid_dsum<2>(acc)) return false;
+      FZ_MARK(ph_gs, sweep_bytes);
+      const double m2 = acc[0] / n, var = acc[1] - acc[0] * m2;
       if (!(var > g * g)) break;  // the sweep annihilated the iterate: keep the previous one
       T *t = A;
       A = B;
@@ -1313,36 +1503,37 @@ struct Eng {
     int done = 0, capped = 0;
     double lastc = 0.0;
     for (int it = 1; it <= kmax; it++) {
-      Red red;
-      red_init(red);
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      double acr[2] = {0.0, 0.0};
       const T muT = (T)mu, sT = (T)s, sigT = (T)sigma;
       for (int i = tid; i < n; i += nthr) {
         const T xi = A[i];
-        T acc = (T)0;
+        T lx = (T)0;
         const int e1 = srp[i + 1];
-        for (int e = srp[i]; e < e1; e++) acc += sw[e] * (xi - A[scol[e]]);
+        for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
         const T xh = (xi - muT) * sT;
-        const T yi = sigT * xh - sT * acc;
+        const T yi = sigT * xh - sT * lx;
         B[i] = yi;
         const double yd = (double)yi, xd = (double)xh;
-        red.s[0] += yd;
-        red.s[1] += yd * yd;
-        red.s[2] += yd * xd;
-        red.s[3] += xd;
+        acc[0] += yd;
+        acc[1] += yd * yd;
+        acc[2] += yd * xd;
+        acc[3] += xd;
         if (resid) {
-          const double lx = (double)sT * (double)acc;
-          red.s[4] += lx * lx;
-          red.s[5] += xd * lx;
+          const double ld = (double)sT * (double)lx;
+          acr[0] += ld * ld;
+          acr[1] += xd * ld;
         }
       }
-      if (!grid_reduce(red)) return false;
-      mark(gs_phase == PH_COARSEST ? PH_COARSEST : PH_PI, sweep_bytes);
-      const double my = red.s[0] / n, var = red.s[1] - red.s[0] * my;
+      if (!grid_dsum<4>(acc)) return false;
+      if (resid && !grid_dsum<2>(acr)) return false;
+      FZ_MARK(ph_pi, sweep_bytes);
+      const double my = acc[0] / n, var = acc[1] - acc[0] * my;
       if (!(var > (g * sigma) * (g * sigma))) break;  // vanished: keep the previous vector
       const double sy = 1.0 / sqrt(var);
-      const double cosv = (red.s[2] - my * red.s[3]) * sy;
+      const double cosv = (acc[2] - my * acc[3]) * sy;
       double rr = 0.0;
-      if (resid) rr = sqrt(fmax(red.s[4] - red.s[5] * red.s[5], 0.0));
+      if (resid) rr = sqrt(fmax(acr[0] - acr[1] * acr[1], 0.0));
       T *t = A;
       A = B;
       B = t;
@@ -1368,14 +1559,15 @@ struct Eng {
 
   // ---- A11: Rayleigh quotient, residual, orthogonality, sign, output --------
   FZD bool finalize() {
+    cur_level = 0;
     Level *L = &S->lv[0];
     const int n = L->n, nnz = L->nnz;
     const int *srp = L->srowptr, *scol = L->scol, *perm = L->perm, *iperm = L->iperm;
     const T *sw = (const T *)L->sw;
     const T *A = (const T *)L->x;
     const double mu = L->mu, s = L->s;
-    Red red;
-    red_init(red);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    IRed big{0, 0, LLONG_MIN};
     for (int k = tid; k < n; k += nthr) {
       const double xk = ((double)A[k] - mu) * s;
       double lx = 0.0, num = 0.0;
@@ -1386,22 +1578,27 @@ struct Eng {
         lx += wv * dl;
         num += wv * dl * dl;
       }
-      red.s[0] += xk * xk;
-      red.s[1] += xk;
-      red.s[2] += num;
-      red.s[3] += lx * lx;
-      const double ax = fabs(xk);
-      const int oi = perm[k];
-      if (ax > red.mx || (ax == red.mx && oi < red.mxi)) {
-        red.mx = ax;
-        red.mxi = oi;
-      }
+      acc[0] += xk * xk;
+      acc[1] += xk;
+      acc[2] += num;
+      acc[3] += lx * lx;
+      big.mx = max(big.mx, (long long)__double_as_longlong(fabs(xk)));
     }
-    if (!grid_reduce(red)) return false;
-    const double xx = red.s[0];
-    const double lam = red.s[2] / (2.0 * xx);
-    const double r2 = red.s[3] / xx - lam * lam;
-    const double xbig = ((double)A[iperm[red.mxi]] - mu) * s;
+    if (!grid_dsum<4>(acc)) return false;
+    if (!grid_ired(big)) return false;
+    // lowest original index among the entries of largest |x|
+    const long long bits = big.mx;
+    IRed low{0, 0, LLONG_MIN};
+    for (int k = tid; k < n; k += nthr) {
+      const double xk = ((double)A[k] - mu) * s;
+      if ((long long)__double_as_longlong(fabs(xk)) == bits) low.mx = max(low.mx, -(long long)perm[k]);
+    }
+    if (!grid_ired(low)) return false;
+    const int imax = (int)(-low.mx);
+    const double xx = acc[0];
+    const double lam = acc[2] / (2.0 * xx);
+    const double r2 = acc[3] / xx - lam * lam;
+    const double xbig = ((double)A[iperm[imax]] - mu) * s;
     const double sign = xbig < 0.0 ? -1.0 : 1.0;
     const double inv = sign / sqrt(xx);
     double *out = S->xout;
@@ -1416,13 +1613,13 @@ struct Eng {
     if (lead()) {
       S->lambda = lam;
       S->residual = sqrt(fmax(r2, 0.0));
-      S->ortho = fabs(red.s[1]) / (sqrt((double)n) * sqrt(xx));
+      S->ortho = fabs(acc[1]) / (sqrt((double)n) * sqrt(xx));
       S->pi_total = ptot;
       S->gs_total = gtot;
       S->capped = cap;
     }
     if (!sync()) return false;
-    mark(PH_FINAL, 4.0 * (n + 1) + (4.0 + sizeof(T)) * nnz + (2.0 * sizeof(T) + 8.0 + 8.0) * n);
+    FZ_MARK(PH_FINAL, 4.0 * (n + 1) + (4.0 + sizeof(T)) * nnz + (2.0 * sizeof(T) + 8.0 + 8.0) * n);
     return true;
   }
 
@@ -1498,6 +1695,7 @@ FZD void engine_entry(State *S, int mode) {
   E.init(S);
   E.run(mode);
   E.persist();
+  E.flush_profile();
 }
 
 }  // namespace fz

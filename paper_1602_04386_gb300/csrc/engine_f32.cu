@@ -13,8 +13,8 @@ void kernels_f32(KernelSet *k) {
   k->grid_solve = (const void *)fz_grid_solve_f32;
   k->cta = (const void *)fz_cta_f32;
   k->names[0] = "fz_grid_setup_f32";
-  k->names[1] = "fz_grid_solve_f32";
-  k->names[2] = "fz_cta_f32";
+  k->names[1] = "fz_cta_f32";
+  k->names[2] = "fz_grid_solve_f32";
 }
 
 }  // namespace fz

@@ -10,7 +10,7 @@ namespace fz {
 constexpr int kMaxLevels = 32;
 constexpr int kMaxBlocks = 2048;   // grid-wide kernel blocks (partials buffer size)
 constexpr int kMaxColors = 1024;   // colour classes per level supported by the reorder
-constexpr int kCtaThreads = 1024;  // one-block kernel
+constexpr int kCtaThreads = 512;   // one-block kernel
 constexpr int kGridThreads = 512;  // grid-wide kernel block size
 
 enum Phase {
@@ -70,12 +70,11 @@ struct Level {
   double last_cos;
 };
 
-struct Red {               // per-block partials of a grid reduction (72 bytes)
-  double s[6];
-  double mx;
-  long long cnt;
-  int mxi;
-  int pad;
+constexpr int kDSum = 6;   // doubles per block partial of a floating-point grid sum
+
+struct IRed {              // per-block partials of an integer grid reduction
+  long long a, b;          // sums (prefix over lower blocks available for both)
+  long long mx;            // maximum (also used for non-negative doubles by bit pattern)
 };
 
 struct State {
@@ -101,18 +100,24 @@ struct State {
   char *scratch;
   unsigned long long scratch_size;
   double *xout;            // device output (n0 doubles), original numbering
-  Red *part;               // [2][kMaxBlocks] partials
+  IRed *ipart;             // [2][kMaxBlocks] integer partials
+  double *dpart;           // [2][kMaxBlocks][kDSum] floating-point partials
+  long long *amax;         // [2][kMaxBlocks] argmax partials: (|x| bits, index) packed by the final pass
+  int wl_cnt[4];           // worklist counters (rotating)
+  int col_max;             // largest colour of the level being coloured
   // results
   double lambda, residual, ortho;
   int pi_total, gs_total;
-  // grid barrier: arrival count, generation, verdict of the last completed barrier
-  unsigned bar_count, bar_gen;
-  int bar_ok;
+  // grid barrier: one word whose top bit flips when every block has arrived;
+  // failword = (barriers passed by the failing block << 32) | status code
+  unsigned bar_word;
   int pad2;
+  unsigned long long failword;
   // device-timer profile: [0] grid-wide kernel, [1] one-block kernel
   unsigned long long t_last;
   double phase_ns[2][PH_COUNT];
   double phase_bytes[2][PH_COUNT];
+  double level_ns[kMaxLevels][PH_COUNT];  // device time per level and phase
   Level lv[kMaxLevels];
 };
 

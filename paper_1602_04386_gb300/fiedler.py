@@ -108,6 +108,7 @@ class fiedler_level_info(C.Structure):
         ("pi_iters", C.c_int),
         ("sigma", C.c_double),
         ("last_cos", C.c_double),
+        ("phase_ms", C.c_float * 16),
     ]
 
 

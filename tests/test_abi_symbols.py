@@ -60,6 +60,7 @@ int main(void){
         sizeof(fiedler_level_info), sizeof(fiedler_profile));
  printf("%zu %zu %zu %zu\n", offsetof(fiedler_options, seed), offsetof(fiedler_result, x),
         offsetof(fiedler_result, bad_index), offsetof(fiedler_profile, phase_bytes));
+ printf("%zu\n", offsetof(fiedler_level_info, phase_ms));
  return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
@@ -69,7 +70,8 @@ int main(void){
         subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe])
         out = subprocess.check_output([exe]).decode().split()
     sizes = [int(v) for v in out[:5]]
-    offs = [int(v) for v in out[5:]]
+    offs = [int(v) for v in out[5:9]]
+    assert int(out[9]) == fiedler.fiedler_level_info.phase_ms.offset
     assert sizes == [C.sizeof(fiedler.fiedler_options), C.sizeof(fiedler.fiedler_graph),
                      C.sizeof(fiedler.fiedler_result), C.sizeof(fiedler.fiedler_level_info),
                      C.sizeof(fiedler.fiedler_profile)]
