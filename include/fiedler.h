@@ -114,7 +114,7 @@ typedef struct fiedler_plan fiedler_plan;
 /* Fills opts with the defaults: FP32_FP64RED, coarse_max_n 25, max_levels 30,
  * stall_ratio 0.9, gs_sweeps 2, pi_max_iters 10000, pi_max_iters_coarsest
  * 100000, pi_cos_tol 1e-6, resid_tol 0, hashed ties, seed 20160214,
- * validate 1, tail_max_n 8192, barrier_timeout_ms 5000, fault_inject 0. */
+ * validate 1, tail_max_n 4096, barrier_timeout_ms 5000, fault_inject 0. */
 void fiedler_options_default(fiedler_options *opts);
 
 /* Creates a plan on the current CUDA device.  opts may be NULL (defaults);

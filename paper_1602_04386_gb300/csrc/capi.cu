@@ -119,11 +119,10 @@ size_t arena_estimate(int64_t n, int64_t nnz, size_t tsz, bool wf64) {
 }
 
 size_t scratch_estimate(int64_t n, int64_t nnz, int nblocks) {
-  // colouring: cround + 3 worklists + colour histogram; matching: cand + 3
-  // worklists (both released before the Galerkin scratch is taken, but sized
-  // together for simplicity); Galerkin: 9 per-vertex/per-aggregate arrays and
-  // (J, slot) keys + FP64 weights per cross entry
-  double b = 4.0 * n * 4 + 4.0 * fz::kMaxColors * nblocks + 4.0 * n * 4 + 4.0 * (n + 1) * 9 + 16.0 * nnz +
+  // one level's scratch, all live at once: colouring (cround + 3 worklists),
+  // matching (cand + 3 worklists), Galerkin (9 per-vertex / per-aggregate
+  // arrays, (J, slot) keys + FP64 weights per cross entry), colour histogram
+  double b = 16.0 * n + 16.0 * n + 4.0 * (n + 1) * 9 + 16.0 * nnz + 4.0 * fz::kMaxColors * nblocks +
              64.0 * 256.0 + (1 << 20);
   return (size_t)b;
 }
@@ -397,7 +396,7 @@ void fiedler_options_default(fiedler_options *o) {
   o->tie_rule = FIEDLER_TIE_HASHED;
   o->seed = 20160214ull;
   o->validate = 1;
-  o->tail_max_n = 8192;
+  o->tail_max_n = 4096;
   o->barrier_timeout_ms = 5000;
   o->fault_inject = 0;
 }

@@ -103,6 +103,7 @@ FZD void best_set(Best &b, uint64_t wk, int u, int v) {
 // per kernel
 constexpr int kShSort = 2048;  // u64 words of the raw buffer (16 KB)
 constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one thread
+constexpr int kTinyN = 256;    // levels up to this size are smoothed by one warp
 
 FZD uint64_t *sh_raw() {
   __shared__ uint64_t raw[kShSort];
@@ -225,6 +226,15 @@ FZD void block_dsum(double (&v)[K]) {
   __syncthreads();
 }
 
+// FP64 warp sum of K values by a fixed xor tree; result in every lane
+template <int K>
+FZD void warp_dsum(double (&v)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; k++)
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
 // ---------------------------------------------------------------------------
 // sorting of short segments: one thread (insertion) or one block (bitonic
 // network for any length: merge blocks start with a reversed-partner step, so
@@ -299,6 +309,20 @@ struct GalerkinScratch {
   double *segw;
 };
 
+// Jones-Plassmann colouring of one level, advanced one round per barrier
+// (see Eng::jp_start); one copy per block in shared memory, written by
+// thread 0 behind a block barrier
+struct JPState {
+  int active, ready, l, r, n, lo, hi;
+  int *cround, *color;
+  int *list[3];
+  long long visits;
+};
+FZD JPState &jps() {
+  __shared__ JPState s;
+  return s;
+}
+
 template <class T, bool GRID>
 struct Eng {
   State *S;
@@ -330,6 +354,7 @@ struct Eng {
     t_last = 0;
     ngen = 0;
     cur_level = 0;
+    if (threadIdx.x == 0) jps().active = 0;
     if (bid == 0) {
       for (int i = threadIdx.x; i < 2 * PH_COUNT + kMaxLevels * PH_COUNT; i += blockDim.x) sh_prof()[i] = 0.0;
       if (threadIdx.x == 0) t_last = gtime();
@@ -392,7 +417,28 @@ struct Eng {
   // (barrier_timeout_ns), and a verdict every block agrees on: a failure
   // counts at this barrier only if it was raised before it (failword carries
   // the number of barriers the failing block had passed).
-  FZD bool sync() {
+  // plain barrier
+  FZD bool sync() { return barrier(); }
+
+  // barrier that also advances the colouring of the level being set up by one
+  // round (used inside the matching, aggregation and Galerkin steps only)
+  FZD bool sync_p() {
+    JPState &jp = jps();
+    if (jp.active && jp.ready) jp_round();
+    const bool ok = barrier();
+    if (ok && jp.active) {
+      if (!jp.ready) {
+        __syncthreads();
+        if (threadIdx.x == 0) jp.ready = 1;
+        __syncthreads();
+      } else {
+        jp_after();
+      }
+    }
+    return ok;
+  }
+
+  FZD bool barrier() {
     if (!GRID) return __syncthreads_and(status() == 0);
     __shared__ int s_ok;
     __syncthreads();
@@ -451,13 +497,14 @@ struct Eng {
 
   // Integer grid reduction: sums a, b and maximum mx; pre_a / pre_b receive
   // the sums over the blocks before this one (chunked scans).
+  template <bool PUMP = false>
   FZD bool grid_ired(IRed &r, long long *pre_a = nullptr, long long *pre_b = nullptr) {
     block_ired(r);
     long long pa = 0, pb = 0;
     if (GRID) {
       IRed *part = S->ipart + rb * kMaxBlocks;
       if (threadIdx.x == 0) part[bid] = r;
-      if (!sync()) return false;
+      if (!(PUMP ? sync_p() : sync())) return false;
       long long *s = sh_ll();
       if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
@@ -497,7 +544,7 @@ struct Eng {
       __syncthreads();
       rb ^= 1;
     } else {
-      if (!__syncthreads_and(status() == 0)) return false;
+      if (!(PUMP ? sync_p() : sync())) return false;
     }
     if (pre_a) *pre_a = pa;
     if (pre_b) *pre_b = pb;
@@ -675,18 +722,21 @@ struct Eng {
   }
 
   // ---- A6: Jones-Plassmann colouring, priority (h(v), v) --------------------
-  // Each block owns the vertices of its chunk and keeps its own worklists
-  // (three rotating lists inside the chunk's range, counters in shared
-  // memory).  Round r reads list r%3 (the whole chunk in round 0) and appends
-  // the vertices still uncoloured to list (r+1)%3; one global atomic per block
-  // per round sums the survivors for the termination test, and the global
-  // counter of list (r+2)%3 is cleared meanwhile (nobody uses it in round r).
-  FZD bool colour(int l) {
+  // The colouring of level l runs alongside the matching, aggregation and
+  // Galerkin steps of the same level (they do not depend on it): jp_start()
+  // sets it up, and every barrier of those steps does one round first
+  // (jp_round) and reads the round's outcome after passing (jp_after).  A round
+  // colours every uncoloured vertex whose priority beats all neighbours still
+  // uncoloured at the start of the round, with the smallest colour unused by
+  // its neighbours coloured earlier.  Each block owns the vertices of its
+  // chunk and keeps its own worklists (three rotating lists inside the chunk's
+  // range, counters in shared memory); one global atomic per block per round
+  // sums the survivors for the termination test, and the global counter of
+  // list (r+2)%3 is cleared meanwhile (nobody uses it in round r).
+  FZD bool jp_start(int l) {
     cur_level = l;
     Level *L = &S->lv[l];
     const int n = L->n;
-    const int *rp = L->rowptr, *ci = L->col;
-    soff = 0;
     int *cround = (int *)salloc(4ull * n);
     int *list[3];
     for (int k = 0; k < 3; k++) list[k] = (int *)salloc(4ull * n);
@@ -694,8 +744,9 @@ struct Eng {
     if (!cround || !list[0] || !list[1] || !list[2] || !color) return false;
     int lo, hi;
     chunk(n, lo, hi);
-    int *s_cnt = sh_ints();  // [0..2] block list counters, [3] block colour max
+    int *s_cnt = sh_ints() + 4;  // [0..2] block list counters, [3] block colour max
     for (int v = tid; v < n; v += nthr) cround[v] = INT_MAX;
+    __syncthreads();
     if (threadIdx.x == 0) {
       s_cnt[0] = hi - lo;
       s_cnt[1] = 0;
@@ -703,79 +754,118 @@ struct Eng {
       s_cnt[3] = -1;
     }
     if (lead()) {
-      S->wl_cnt[1] = 0;
-      S->wl_cnt[2] = 0;
+      S->jp_cnt[1] = 0;
+      S->jp_cnt[2] = 0;
       S->col_max = -1;
+      L->color = color;
     }
-    if (!sync()) return false;
-    int r = 0;
-    long long visits = 0;
-    for (;; r++) {
-      const int cur = r % 3, nxt = (r + 1) % 3, clr = (r + 2) % 3;
-      if (lead() && r > 0) S->wl_cnt[clr] = 0;
-      const int cnt = s_cnt[cur];
-      for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const int v = r == 0 ? lo + q : list[cur][lo + q];
-        const uint64_t hv = vtx_hash(v);
-        bool top = true;
-        const int e0 = rp[v], e1 = rp[v + 1];
-        for (int e = e0; e < e1; e++) {
-          const int u = ci[e];
-          if (cround[u] >= r) {
-            const uint64_t hu = vtx_hash(u);
-            if (hu > hv || (hu == hv && u > v)) {
-              top = false;
-              break;
-            }
-          }
-        }
-        if (!top) {
-          list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
-          continue;
-        }
-        int base = 0, c = 0;
-        for (;;) {
-          uint64_t m = 0;
-          for (int e = e0; e < e1; e++) {
-            const int u = ci[e];
-            if (cround[u] < r) {
-              const int cu = color[u] - base;
-              if (cu >= 0 && cu < 64) m |= 1ull << cu;
-            }
-          }
-          if (m != ~0ull) {
-            c = base + __ffsll((long long)~m) - 1;
+    if (threadIdx.x == 0) {
+      JPState &jp = jps();
+      jp.active = 1;
+      jp.ready = 0;
+      jp.l = l;
+      jp.r = 0;
+      jp.n = n;
+      jp.lo = lo;
+      jp.hi = hi;
+      jp.cround = cround;
+      jp.color = color;
+      for (int k = 0; k < 3; k++) jp.list[k] = list[k];
+      jp.visits = 0;
+    }
+    __syncthreads();
+    return true;
+  }
+
+  FZD void jp_round() {
+    JPState &jp = jps();
+    const Level *L = &S->lv[jp.l];
+    const int *rp = L->rowptr, *ci = L->col;
+    int *cround = jp.cround, *color = jp.color;
+    const int r = jp.r, lo = jp.lo;
+    const int cur = r % 3, nxt = (r + 1) % 3, clr = (r + 2) % 3;
+    int *s_cnt = sh_ints() + 4;
+    if (lead() && r > 0) S->jp_cnt[clr] = 0;
+    const int cnt = s_cnt[cur];
+    int *lcur = jp.list[cur], *lnxt = jp.list[nxt];
+    // threads in reverse order, so that on small levels the colouring runs on
+    // other warps than the step it accompanies
+    for (int q = blockDim.x - 1 - threadIdx.x; q < cnt; q += blockDim.x) {
+      const int v = r == 0 ? lo + q : lcur[lo + q];
+      const uint64_t hv = vtx_hash(v);
+      bool top = true;
+      const int e0 = rp[v], e1 = rp[v + 1];
+      for (int e = e0; e < e1; e++) {
+        const int u = ci[e];
+        if (cround[u] >= r) {
+          const uint64_t hu = vtx_hash(u);
+          if (hu > hv || (hu == hv && u > v)) {
+            top = false;
             break;
           }
-          base += 64;
         }
-        color[v] = c;
-        cround[v] = r;
-        atomicMax(&s_cnt[3], c);
       }
+      if (!top) {
+        lnxt[lo + atomicAdd(&s_cnt[nxt], 1)] = v;
+        continue;
+      }
+      int base = 0, c = 0;
+      for (;;) {
+        uint64_t m = 0;
+        for (int e = e0; e < e1; e++) {
+          const int u = ci[e];
+          if (cround[u] < r) {
+            const int cu = color[u] - base;
+            if (cu >= 0 && cu < 64) m |= 1ull << cu;
+          }
+        }
+        if (m != ~0ull) {
+          c = base + __ffsll((long long)~m) - 1;
+          break;
+        }
+        base += 64;
+      }
+      color[v] = c;
+      cround[v] = r;
+      atomicMax(&s_cnt[3], c);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (s_cnt[nxt]) atomicAdd(&S->jp_cnt[nxt], s_cnt[nxt]);
+      if (s_cnt[3] >= 0) atomicMax(&S->col_max, s_cnt[3]);
+      s_cnt[cur] = 0;  // becomes the append target of round r + 2
+      jp.visits += cnt;
+    }
+  }
+
+  FZD void jp_after() {
+    JPState &jp = jps();
+    const int r = jp.r, l = jp.l;
+    const int left = *(volatile int *)&S->jp_cnt[(r + 1) % 3];
+    __syncthreads();
+    if (left != 0) {
+      if (threadIdx.x == 0) jp.r = r + 1;
       __syncthreads();
-      if (threadIdx.x == 0) {
-        if (s_cnt[nxt]) atomicAdd(&S->wl_cnt[nxt], s_cnt[nxt]);
-        s_cnt[cur] = 0;  // becomes the append target of round r + 2
-      }
-      visits += cnt;
-      if (!sync()) return false;
-      if (wl_read(nxt) == 0) break;
+      return;
     }
-    if (threadIdx.x == 0 && s_cnt[3] >= 0) atomicMax(&S->col_max, s_cnt[3]);
-    if (!sync()) return false;
     const int ncol = *(volatile int *)&S->col_max + 1;
-    if (ncol > kMaxColors) {
-      fail(ST_ENOTSUP);
-      return false;
-    }
+    if (ncol > kMaxColors) fail(ST_ENOTSUP);
     if (lead()) {
-      L->color = color;
+      Level *L = &S->lv[l];
       L->ncolors = ncol;
       L->color_rounds = r + 1;
     }
-    if (!sync()) return false;
-    FZ_MARK(PH_COLOR, 8.0 * n + (double)visits * 12.0 * nb + 4.0 * L->nnz);
+    if (threadIdx.x == 0) jp.active = 0;
+    __syncthreads();
+  }
+
+  // run the remaining colouring rounds on their own barriers
+  FZD bool jp_finish() {
+    while (jps().active)
+      if (!sync_p()) return false;
+    if (!sync()) return false;  // publishes ncolors / color_rounds
+    const Level *L = &S->lv[jps().l];
+    FZ_MARK(PH_COLOR, 8.0 * L->n + (double)jps().visits * 12.0 * nb + 4.0 * L->nnz);
     return true;
   }
 
@@ -960,7 +1050,7 @@ struct Eng {
       S->wl_cnt[2] = 0;
     }
     for (int v = tid; v < n; v += nthr) mate[v] = -1;
-    if (!sync()) return false;
+    if (!sync_p()) return false;
     int rounds = 0;
     long long visits = 0;
     for (int ph = 0;; ph++) {
@@ -997,7 +1087,7 @@ struct Eng {
         s_cnt[cur] = 0;
       }
       visits += cnt;
-      if (!sync()) return false;
+      if (!sync_p()) return false;
       const int total = wl_read(nxt);
       if ((ph & 1) == 0) {
         if (total == 0) break;
@@ -1010,7 +1100,7 @@ struct Eng {
       L->mate = mate;
       L->match_rounds = rounds;
     }
-    if (!sync()) return false;
+    if (!sync_p()) return false;
     FZ_MARK(PH_MATCH, 4.0 * n + (double)visits * nb * (8.0 + 4.0 * 4 + (L->w64 ? 8.0 : 4.0) * 4));
     return true;
   }
@@ -1032,7 +1122,7 @@ struct Eng {
       red.a += (m >= 0) ? (v < m) : (rp[v + 1] == rp[v]);
     }
     long long pre = 0;
-    if (!grid_ired(red, &pre)) return false;
+    if (!grid_ired<true>(red, &pre)) return false;
     const long long nc = red.a;
     nc_out = -1;
     if (nc < 2 || (double)nc > stall * (double)n) return true;
@@ -1067,7 +1157,7 @@ struct Eng {
       G.fill[I] = 0;
       G.tcnt[I] = 0;
     }
-    if (!sync()) return false;
+    if (!sync_p()) return false;
     for (int v = tid; v < n; v += nthr) {
       const int m = mate[v];
       int a;
@@ -1099,7 +1189,7 @@ struct Eng {
       L->agg = agg;
       L->nc = (int)nc;
     }
-    if (!sync()) return false;
+    if (!sync_p()) return false;
     FZ_MARK(PH_AGG, 24.0 * n + 12.0 * L->nnz);
     nc_out = (int)nc;
     return true;
@@ -1121,7 +1211,7 @@ struct Eng {
       G.cc[v] = k;
       if (k) atomicAdd(&G.tcnt[I], k);
     }
-    if (!sync()) return false;
+    if (!sync_p()) return false;
     // G2: member and segment pointers (chunked scans over aggregates)
     int lo, hi;
     chunk(nc, lo, hi);
@@ -1131,7 +1221,7 @@ struct Eng {
       red.b += G.tcnt[I];
     }
     long long preA = 0, preB = 0;
-    if (!grid_ired(red, &preA, &preB)) return false;
+    if (!grid_ired<true>(red, &preA, &preB)) return false;
     const long long ttot = red.b;
     {
       long long ra = preA, rbb = preB;
@@ -1156,14 +1246,14 @@ struct Eng {
     G.keys = (uint64_t *)salloc(8ull * (ttot > 0 ? ttot : 1));
     G.segw = (double *)salloc(8ull * (ttot > 0 ? ttot : 1));
     if (!G.keys || !G.segw) return false;
-    if (!sync()) return false;
+    if (!sync_p()) return false;
     // G3: members of each aggregate
     for (int v = tid; v < n; v += nthr) {
       const int I = agg[v];
       const int s = atomicAdd(&G.fill[I], 1);
       G.members[G.aggptr[I] + s] = v;
     }
-    if (!sync()) return false;
+    if (!sync_p()) return false;
     // G4: members ascending; offset of each member's entries inside its segment
     {
       int *s_big = sh_list();
@@ -1206,7 +1296,7 @@ struct Eng {
         __syncthreads();
       }
     }
-    if (!sync()) return false;
+    if (!sync_p()) return false;
     // G5: cross entries into their aggregate's segment, key = (J, slot)
     for (int v = tid; v < n; v += nthr) {
       const int I = agg[v];
@@ -1220,7 +1310,7 @@ struct Eng {
         slot++;
       }
     }
-    if (!sync()) return false;
+    if (!sync_p()) return false;
     // G6: sort each segment by (J, slot); distinct J per coarse row
     red = IRed{0, 0, 0};
     {
@@ -1266,7 +1356,7 @@ struct Eng {
       }
     }
     long long pre = 0;
-    if (!grid_ired(red, &pre)) return false;
+    if (!grid_ired<true>(red, &pre)) return false;
     const long long nnzc = red.a;
     int *crp = (int *)aalloc(4ull * (nc + 1));
     int *ccol = (int *)aalloc(4ull * (nnzc > 0 ? nnzc : 1));
@@ -1346,7 +1436,7 @@ struct Eng {
       }
       if (lead()) crp[nc] = (int)nnzc;
     }
-    if (!grid_ired(red)) return false;
+    if (!grid_ired<true>(red)) return false;
     if (lead()) {
       Level &C = S->lv[l + 1];
       C.n = nc;
@@ -1361,7 +1451,7 @@ struct Eng {
       C.mate = nullptr;
       C.nc = 0;
     }
-    if (!sync()) return false;
+    if (!sync_p()) return false;
     FZ_MARK(PH_GALERKIN, 40.0 * n + (12.0 + 8.0 + 16.0 * 3.0) * L->nnz);
     return true;
   }
@@ -1453,6 +1543,7 @@ struct Eng {
 
   // ---- A9 + A10: Gauss-Seidel sweeps, then shifted power iteration ----------
   FZD bool smooth(int l, int kmax, double mu, double s, int gs_phase) {
+    if (!GRID && S->lv[l].n <= kTinyN) return smooth_warp(l, kmax, mu, s, gs_phase);
     Level *L = &S->lv[l];
     const int n = L->n, nnz = L->nnz, C = L->ncolors;
     const int *srp = L->srowptr, *scol = L->scol, *cst = L->colstart;
@@ -1557,6 +1648,118 @@ struct Eng {
     return sync();
   }
 
+  // The same Gauss-Seidel sweeps and power iteration for tiny levels
+  // (n <= kTinyN, one-block kernel only): warp 0 runs them alone, with warp
+  // syncs between colour passes and warp-shuffle FP64 sums, while the other
+  // warps wait at one block barrier.  Identical arithmetic per row; only the
+  // order of the FP64 sums differs from smooth().
+  FZD bool smooth_warp(int l, int kmax, double mu, double s, int gs_phase) {
+    Level *L = &S->lv[l];
+    const int n = L->n, nnz = L->nnz, C = L->ncolors;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const int *srp = L->srowptr, *scol = L->scol, *cst = L->colstart;
+      const T *sw = (const T *)L->sw;
+      T *A = (T *)L->x, *B = (T *)L->y;
+      const double g = S->opt.guard;
+      const int nsweeps = S->opt.gs_sweeps;
+      const double sweep_bytes = 4.0 * (n + 1) + (4.0 + sizeof(T)) * nnz + 2.0 * sizeof(T) * n;
+      const int ph_gs = gs_phase == PH_COARSEST ? PH_COARSEST : PH_GS;
+      const int ph_pi = gs_phase == PH_COARSEST ? PH_COARSEST : PH_PI;
+      int sweeps = 0;
+      for (int k = 0; k < nsweeps; k++) {
+        double acc[2] = {0.0, 0.0};
+        const T muT = (T)mu, sT = (T)s;
+        for (int c = 0; c < C; c++) {
+          const int cs = cst[c], ce = cst[c + 1];
+          for (int i = cs + lane; i < ce; i += 32) {
+            T num = (T)0, dsum = (T)0;
+            const int e1 = srp[i + 1];
+            for (int e = srp[i]; e < e1; e++) {
+              const int j = scol[e];
+              const T wv = sw[e];
+              const T xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
+              num += wv * xj;
+              dsum += wv;
+            }
+            const T xi = num / dsum;
+            B[i] = xi;
+            acc[0] += (double)xi;
+            acc[1] += (double)xi * (double)xi;
+          }
+          __syncwarp();
+        }
+        warp_dsum<2>(acc);
+        FZ_MARK(ph_gs, sweep_bytes);
+        const double m2 = acc[0] / n, var = acc[1] - acc[0] * m2;
+        if (!(var > g * g)) break;
+        T *t = A;
+        A = B;
+        B = t;
+        mu = m2;
+        s = 1.0 / sqrt(var);
+        sweeps++;
+      }
+      const double sigma = L->sigma;
+      const double tol = S->opt.pi_cos_tol, rtol = S->opt.resid_tol;
+      const bool resid = rtol > 0.0;
+      int done = 0, capped = 0;
+      double lastc = 0.0;
+      for (int it = 1; it <= kmax; it++) {
+        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        const T muT = (T)mu, sT = (T)s, sigT = (T)sigma;
+        for (int i = lane; i < n; i += 32) {
+          const T xi = A[i];
+          T lx = (T)0;
+          const int e1 = srp[i + 1];
+          for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
+          const T xh = (xi - muT) * sT;
+          const T yi = sigT * xh - sT * lx;
+          B[i] = yi;
+          const double yd = (double)yi, xd = (double)xh;
+          acc[0] += yd;
+          acc[1] += yd * yd;
+          acc[2] += yd * xd;
+          acc[3] += xd;
+          if (resid) {
+            const double ld = (double)sT * (double)lx;
+            acc[4] += ld * ld;
+            acc[5] += xd * ld;
+          }
+        }
+        __syncwarp();
+        warp_dsum<6>(acc);
+        FZ_MARK(ph_pi, sweep_bytes);
+        const double my = acc[0] / n, var = acc[1] - acc[0] * my;
+        if (!(var > (g * sigma) * (g * sigma))) break;
+        const double sy = 1.0 / sqrt(var);
+        const double cosv = (acc[2] - my * acc[3]) * sy;
+        double rr = 0.0;
+        if (resid) rr = sqrt(fmax(acc[4] - acc[5] * acc[5], 0.0));
+        T *t = A;
+        A = B;
+        B = t;
+        mu = my;
+        s = sy;
+        lastc = cosv;
+        done = it;
+        if (cosv > 1.0 - tol && (!resid || rr <= rtol * sigma)) break;
+        if (it == kmax) capped = 1;
+      }
+      if (lane == 0) {
+        L->x = A;
+        L->y = B;
+        L->mu = mu;
+        L->s = s;
+        L->gs_sweeps = sweeps;
+        L->pi_iters = done;
+        L->last_cos = lastc;
+        L->capped = capped;
+      }
+    }
+    return sync();
+  }
+
   // ---- A11: Rayleigh quotient, residual, orthogonality, sign, output --------
   FZD bool finalize() {
     cur_level = 0;
@@ -1566,25 +1769,33 @@ struct Eng {
     const T *sw = (const T *)L->sw;
     const T *A = (const T *)L->x;
     const double mu = L->mu, s = L->s;
+    // x_hat = (x - mu) * s.  The edge form needs only differences x_i - x_j,
+    // in which mu cancels: per row, sum_j w (x_i - x_j) and sum_j w (x_i - x_j)^2
+    // are taken in T (neighbouring values of a smooth vector are close, so
+    // their difference is exact in T) and accumulated over rows in FP64, scaled
+    // by s and s^2 at the end.
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     IRed big{0, 0, LLONG_MIN};
     for (int k = tid; k < n; k += nthr) {
-      const double xk = ((double)A[k] - mu) * s;
-      double lx = 0.0, num = 0.0;
+      const T xi = A[k];
+      T lx = (T)0, num = (T)0;
       const int e1 = srp[k + 1];
       for (int e = srp[k]; e < e1; e++) {
-        const double dl = xk - ((double)A[scol[e]] - mu) * s;
-        const double wv = (double)sw[e];
-        lx += wv * dl;
-        num += wv * dl * dl;
+        const T dl = xi - A[scol[e]];
+        const T wd = sw[e] * dl;
+        lx += wd;
+        num += wd * dl;
       }
+      const double xk = ((double)xi - mu) * s;
       acc[0] += xk * xk;
       acc[1] += xk;
-      acc[2] += num;
-      acc[3] += lx * lx;
+      acc[2] += (double)num;
+      acc[3] += (double)lx * (double)lx;
       big.mx = max(big.mx, (long long)__double_as_longlong(fabs(xk)));
     }
     if (!grid_dsum<4>(acc)) return false;
+    acc[2] *= s * s;
+    acc[3] *= s * s;
     if (!grid_ired(big)) return false;
     // lowest original index among the entries of largest |x|
     const long long bits = big.mx;
@@ -1638,25 +1849,25 @@ struct Eng {
         const int l = nlevels - 1;
         const int n = S->lv[l].n;
         if (!elig(n)) return true;
-        if (!colour(l)) return false;
-        if (!reorder(l)) return false;
-        if (n <= S->opt.coarse_max_n || nlevels >= S->opt.max_levels) {
-          setup_done = 1;
-          coarsest = l;
-          persist();
-          break;
-        }
-        if (!match(l)) return false;
+        soff = 0;  // the level's scratch: colouring, matching, Galerkin
+        if (!jp_start(l)) return false;
+        bool last = n <= S->opt.coarse_max_n || nlevels >= S->opt.max_levels;
         GalerkinScratch G;
         int nc = -1;
-        if (!aggregate(l, nc, G)) return false;
-        if (nc < 0) {
+        if (!last) {
+          if (!match(l)) return false;
+          if (!aggregate(l, nc, G)) return false;
+          last = nc < 0;
+          if (!last && !galerkin(l, nc, G)) return false;
+        }
+        if (!jp_finish()) return false;
+        if (!reorder(l)) return false;
+        if (last) {
           setup_done = 1;
           coarsest = l;
           persist();
           break;
         }
-        if (!galerkin(l, nc, G)) return false;
         nlevels++;
         persist();
       }

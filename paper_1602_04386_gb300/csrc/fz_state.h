@@ -103,7 +103,8 @@ struct State {
   IRed *ipart;             // [2][kMaxBlocks] integer partials
   double *dpart;           // [2][kMaxBlocks][kDSum] floating-point partials
   long long *amax;         // [2][kMaxBlocks] argmax partials: (|x| bits, index) packed by the final pass
-  int wl_cnt[4];           // worklist counters (rotating)
+  int wl_cnt[4];           // worklist counters of the matching (rotating)
+  int jp_cnt[4];           // worklist counters of the colouring (rotating)
   int col_max;             // largest colour of the level being coloured
   // results
   double lambda, residual, ortho;
