@@ -121,6 +121,10 @@ FZD long long *sh_ll() {
   __shared__ long long v[3 * 33];
   return v;
 }
+FZD double *sh_bc() {  // scalars computed by one thread, read by the block
+  __shared__ double v[8];
+  return v;
+}
 FZD double *sh_prof() {  // [2][PH_COUNT] totals, then [kMaxLevels][PH_COUNT] per level
   __shared__ double v[2 * PH_COUNT + kMaxLevels * PH_COUNT];
   return v;
@@ -1456,6 +1460,26 @@ struct Eng {
     return true;
   }
 
+  // mean and inverse deflated norm from (sum x, sum x^2), computed by thread 0
+  // and broadcast; false (EDEGEN) if the deflated vector vanished
+  FZD bool deflate_scalars(const double (&acc)[2], int n, double &mu, double &sc) {
+    double *bc = sh_bc();
+    if (threadIdx.x == 0) {
+      const double g = S->opt.guard;
+      const double m = acc[0] / n, var = acc[1] - acc[0] * m;
+      bc[0] = var > g * g ? 1.0 : 0.0;
+      bc[1] = m;
+      bc[2] = var > g * g ? 1.0 / sqrt(var) : 0.0;
+    }
+    __syncthreads();
+    const bool ok = bc[0] != 0.0;
+    mu = bc[1];
+    sc = bc[2];
+    __syncthreads();
+    if (!ok) fail(ST_EDEGEN);
+    return ok;
+  }
+
   // ---- A7: coarsest level: connectivity, random start ---------------------
   FZD bool coarsest_solve(int J) {
     cur_level = J;
@@ -1503,14 +1527,10 @@ struct Eng {
       acc[1] += (double)v * (double)v;
     }
     if (!grid_dsum<2>(acc)) return false;
-    const double mu = acc[0] / n, var = acc[1] - acc[0] * mu;
-    const double g = S->opt.guard;
-    if (!(var > g * g)) {
-      fail(ST_EDEGEN);
-      return false;
-    }
+    double mu, sc;
+    if (!deflate_scalars(acc, n, mu, sc)) return false;
     FZ_MARK(PH_COARSEST, 16.0 * n + 8.0 * L->nnz);
-    return smooth(J, S->opt.pi_max_iters_coarsest, mu, 1.0 / sqrt(var), PH_COARSEST);
+    return smooth(J, S->opt.pi_max_iters_coarsest, mu, sc, PH_COARSEST);
   }
 
   // ---- A8: prolongation y^j = I^T y^{j+1} ----------------------------------
@@ -1520,25 +1540,21 @@ struct Eng {
     const Level *Cl = &S->lv[l + 1];
     const int n = F->n;
     const T *xc = (const T *)Cl->x;
-    const T muc = (T)Cl->mu, sc = (T)Cl->s;
+    const T muc = (T)Cl->mu, scc = (T)Cl->s;
     T *x = (T *)F->x;
     const int *sagg = F->sagg;
     double acc[2] = {0.0, 0.0};
     for (int k = tid; k < n; k += nthr) {
-      const T v = (xc[sagg[k]] - muc) * sc;
+      const T v = (xc[sagg[k]] - muc) * scc;
       x[k] = v;
       acc[0] += (double)v;
       acc[1] += (double)v * (double)v;
     }
     if (!grid_dsum<2>(acc)) return false;
-    const double mu = acc[0] / n, var = acc[1] - acc[0] * mu;
-    const double g = S->opt.guard;
-    if (!(var > g * g)) {
-      fail(ST_EDEGEN);
-      return false;
-    }
+    double mu, sc;
+    if (!deflate_scalars(acc, n, mu, sc)) return false;
     FZ_MARK(PH_PROLONG, (4.0 + 2.0 * sizeof(T)) * n);
-    return smooth(l, S->opt.pi_max_iters, mu, 1.0 / sqrt(var), PH_GS);
+    return smooth(l, S->opt.pi_max_iters, mu, sc, PH_GS);
   }
 
   // ---- A9 + A10: Gauss-Seidel sweeps, then shifted power iteration ----------
@@ -1554,10 +1570,15 @@ struct Eng {
     const double sweep_bytes = 4.0 * (n + 1) + (4.0 + sizeof(T)) * nnz + 2.0 * sizeof(T) * n;
     const int ph_gs = gs_phase == PH_COARSEST ? PH_COARSEST : PH_GS;
     const int ph_pi = gs_phase == PH_COARSEST ? PH_COARSEST : PH_PI;
+    // FP64 scalars (means, norms, cos test) are computed by thread 0 of each
+    // block from the grid totals and broadcast through shared memory; the
+    // T copies used in the inner loops come with them
+    double *bc = sh_bc();
+    const double inv_n = 1.0 / (double)n;
+    T muT = (T)mu, sT = (T)s;
     int sweeps = 0;
     for (int k = 0; k < nsweeps; k++) {
       double acc[2] = {0.0, 0.0};
-      const T muT = (T)mu, sT = (T)s;
       for (int c = 0; c < C; c++) {
         const int cs = cst[c], ce = cst[c + 1];
         for (int i = cs + tid; i < ce; i += nthr) {
@@ -1579,24 +1600,35 @@ struct Eng {
       }
       if (!grid_dsum<2>(acc)) return false;
       FZ_MARK(ph_gs, sweep_bytes);
-      const double m2 = acc[0] / n, var = acc[1] - acc[0] * m2;
-      if (!(var > g * g)) break;  // the sweep annihilated the iterate: keep the previous one
+      if (threadIdx.x == 0) {
+        const double m2 = acc[0] * inv_n, var = acc[1] - acc[0] * m2;
+        bc[0] = var > g * g ? 1.0 : 0.0;  // else: the sweep annihilated the iterate
+        bc[1] = m2;
+        bc[2] = var > g * g ? 1.0 / sqrt(var) : 0.0;
+      }
+      __syncthreads();
+      const bool keep = bc[0] != 0.0;
+      const double m2 = bc[1], s2 = bc[2];
+      __syncthreads();
+      if (!keep) break;  // keep the previous iterate
       T *t = A;
       A = B;
       B = t;
       mu = m2;
-      s = 1.0 / sqrt(var);
+      s = s2;
+      muT = (T)mu;
+      sT = (T)s;
       sweeps++;
     }
     const double sigma = L->sigma;
     const double tol = S->opt.pi_cos_tol, rtol = S->opt.resid_tol;
     const bool resid = rtol > 0.0;
+    const T sigT = (T)sigma;
     int done = 0, capped = 0;
     double lastc = 0.0;
     for (int it = 1; it <= kmax; it++) {
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
       double acr[2] = {0.0, 0.0};
-      const T muT = (T)mu, sT = (T)s, sigT = (T)sigma;
       for (int i = tid; i < n; i += nthr) {
         const T xi = A[i];
         T lx = (T)0;
@@ -1619,20 +1651,33 @@ struct Eng {
       if (!grid_dsum<4>(acc)) return false;
       if (resid && !grid_dsum<2>(acr)) return false;
       FZ_MARK(ph_pi, sweep_bytes);
-      const double my = acc[0] / n, var = acc[1] - acc[0] * my;
-      if (!(var > (g * sigma) * (g * sigma))) break;  // vanished: keep the previous vector
-      const double sy = 1.0 / sqrt(var);
-      const double cosv = (acc[2] - my * acc[3]) * sy;
-      double rr = 0.0;
-      if (resid) rr = sqrt(fmax(acr[0] - acr[1] * acr[1], 0.0));
+      if (threadIdx.x == 0) {
+        const double my = acc[0] * inv_n, var = acc[1] - acc[0] * my;
+        const bool ok = var > (g * sigma) * (g * sigma);  // else the step vanished
+        const double sy = ok ? 1.0 / sqrt(var) : 0.0;
+        const double cosv = (acc[2] - my * acc[3]) * sy;
+        const double rr = resid ? sqrt(fmax(acr[0] - acr[1] * acr[1], 0.0)) : 0.0;
+        bc[0] = ok ? 1.0 : 0.0;
+        bc[1] = my;
+        bc[2] = sy;
+        bc[3] = cosv;
+        bc[4] = (ok && cosv > 1.0 - tol && (!resid || rr <= rtol * sigma)) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      const bool ok = bc[0] != 0.0, stop = bc[4] != 0.0;
+      const double my = bc[1], sy = bc[2], cosv = bc[3];
+      __syncthreads();
+      if (!ok) break;  // keep the previous vector
       T *t = A;
       A = B;
       B = t;
       mu = my;
       s = sy;
+      muT = (T)mu;
+      sT = (T)s;
       lastc = cosv;
       done = it;
-      if (cosv > 1.0 - tol && (!resid || rr <= rtol * sigma)) break;
+      if (stop) break;
       if (it == kmax) capped = 1;
     }
     if (lead()) {
@@ -1691,13 +1736,23 @@ struct Eng {
         }
         warp_dsum<2>(acc);
         FZ_MARK(ph_gs, sweep_bytes);
-        const double m2 = acc[0] / n, var = acc[1] - acc[0] * m2;
-        if (!(var > g * g)) break;
+        double m2 = 0.0, s2 = 0.0;
+        int keep = 0;
+        if (lane == 0) {
+          m2 = acc[0] / n;
+          const double var = acc[1] - acc[0] * m2;
+          keep = var > g * g;
+          s2 = keep ? 1.0 / sqrt(var) : 0.0;
+        }
+        keep = __shfl_sync(0xffffffffu, keep, 0);
+        m2 = __shfl_sync(0xffffffffu, m2, 0);
+        s2 = __shfl_sync(0xffffffffu, s2, 0);
+        if (!keep) break;
         T *t = A;
         A = B;
         B = t;
         mu = m2;
-        s = 1.0 / sqrt(var);
+        s = s2;
         sweeps++;
       }
       const double sigma = L->sigma;
@@ -1730,12 +1785,23 @@ struct Eng {
         __syncwarp();
         warp_dsum<6>(acc);
         FZ_MARK(ph_pi, sweep_bytes);
-        const double my = acc[0] / n, var = acc[1] - acc[0] * my;
-        if (!(var > (g * sigma) * (g * sigma))) break;
-        const double sy = 1.0 / sqrt(var);
-        const double cosv = (acc[2] - my * acc[3]) * sy;
-        double rr = 0.0;
-        if (resid) rr = sqrt(fmax(acc[4] - acc[5] * acc[5], 0.0));
+        double my = 0.0, sy = 0.0, cosv = 0.0;
+        int ok = 0, stop = 0;
+        if (lane == 0) {
+          my = acc[0] / n;
+          const double var = acc[1] - acc[0] * my;
+          ok = var > (g * sigma) * (g * sigma);
+          sy = ok ? 1.0 / sqrt(var) : 0.0;
+          cosv = (acc[2] - my * acc[3]) * sy;
+          const double rr = resid ? sqrt(fmax(acc[4] - acc[5] * acc[5], 0.0)) : 0.0;
+          stop = ok && cosv > 1.0 - tol && (!resid || rr <= rtol * sigma);
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        my = __shfl_sync(0xffffffffu, my, 0);
+        sy = __shfl_sync(0xffffffffu, sy, 0);
+        cosv = __shfl_sync(0xffffffffu, cosv, 0);
+        if (!ok) break;
         T *t = A;
         A = B;
         B = t;
@@ -1743,7 +1809,7 @@ struct Eng {
         s = sy;
         lastc = cosv;
         done = it;
-        if (cosv > 1.0 - tol && (!resid || rr <= rtol * sigma)) break;
+        if (stop) break;
         if (it == kmax) capped = 1;
       }
       if (lane == 0) {
