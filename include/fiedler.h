@@ -202,6 +202,36 @@ fiedler_status fiedler_plan_set_profiling(fiedler_plan *plan, int on);
 /* Counters of the last solve. */
 fiedler_status fiedler_plan_get_profile(const fiedler_plan *plan, fiedler_profile *out);
 
+/* ---- solve without allocation ------------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory (code running inside a memory pool or
+ * cap owned by someone else, plug-ins that must not grow the device
+ * footprint after start-up, latency-critical paths where allocation is
+ * forbidden).  It solves one graph like fiedler_solve, but all its working
+ * memory (solve state, hierarchy, scratch) is one fixed 16 MiB device array
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits.  It calls no cudaMalloc / cudaFree and no allocating library
+ * routine, and needs no plan.
+ *  - graph: device-resident inputs (on_device = 1), else EINVAL.
+ *  - x: device output of n doubles (may be NULL).  opts may be NULL.
+ *  - cuda_stream: stream the work is ordered on (NULL = legacy default stream);
+ *    the call returns after that work has finished.
+ *  - Size limit: graphs whose hierarchy cannot fit the array (roughly beyond
+ *    80k vertices / 300k stored entries) are refused with FIEDLER_ENOTSUP
+ *    before any work is queued; a hierarchy that still outgrows it at run time
+ *    also returns FIEDLER_ENOTSUP.
+ *  - Every call reuses the same array and overwrites the previous call's
+ *    contents (the state is rewritten at the start of each call), so calls must
+ *    not overlap on the GPU: the library serialises callers within a process.
+ *  - The first call on each device looks up the array's device address with
+ *    cudaGetSymbolAddress (with that device current); make that first call
+ *    before any stream capture begins.
+ *  - Every level runs in the one-block engine, so results equal those of
+ *    fiedler_solve with tail_max_n at least n. */
+fiedler_status fiedler_solve_noalloc(const fiedler_options *opts, const fiedler_graph *graph, double *x,
+                                     void *cuda_stream, fiedler_result *result);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,7 +43,7 @@ SYMBOLS = (
     "fiedler_options_default", "fiedler_plan_create", "fiedler_solve", "fiedler_batch_submit",
     "fiedler_poll", "fiedler_cancel", "fiedler_plan_destroy", "fiedler_status_str",
     "fiedler_plan_num_levels", "fiedler_plan_level_info", "fiedler_plan_copy_level",
-    "fiedler_plan_set_profiling", "fiedler_plan_get_profile",
+    "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc",
 )
 
 
@@ -163,9 +163,11 @@ def load():
         L.fiedler_plan_copy_level.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
         L.fiedler_plan_set_profiling.argtypes = [vp, C.c_int]
         L.fiedler_plan_get_profile.argtypes = [vp, C.POINTER(fiedler_profile)]
+        L.fiedler_solve_noalloc.argtypes = [C.POINTER(fiedler_options), C.POINTER(fiedler_graph), vp, vp,
+                                            C.POINTER(fiedler_result)]
         for f in ("fiedler_plan_create", "fiedler_solve", "fiedler_batch_submit", "fiedler_poll", "fiedler_cancel",
                   "fiedler_plan_num_levels", "fiedler_plan_level_info", "fiedler_plan_copy_level",
-                  "fiedler_plan_set_profiling", "fiedler_plan_get_profile"):
+                  "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -234,6 +236,12 @@ def fiedler_plan_get_profile(plan):
     pr = fiedler_profile()
     st = load().fiedler_plan_get_profile(plan, C.byref(pr))
     return st, pr
+
+
+def fiedler_solve_noalloc(opts: fiedler_options | None, graph: fiedler_graph, x_dev_ptr, cuda_stream,
+                          result: fiedler_result) -> int:
+    return load().fiedler_solve_noalloc(C.byref(opts) if opts is not None else None, C.byref(graph), x_dev_ptr,
+                                        cuda_stream, C.byref(result))
 
 
 # ------------------------------------------------------------ convenience
