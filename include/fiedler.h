@@ -80,6 +80,9 @@ typedef struct {
   int barrier_timeout_ms;    /* bound on every device-side wait (grid barriers) */
   int fault_inject;          /* testing only: 1 = one block skips the first grid barrier, so the
                                 others' bounded wait runs out and the solve reports ETIMEOUT */
+  size_t hbm_budget_bytes;   /* serving: device memory the in-flight tickets may hold (0 = 16 GiB) */
+  int max_batch;             /* serving: most tickets per batched launch */
+  int max_inflight;          /* serving: batched launches in flight at once (1..4) */
 } fiedler_options;
 
 typedef struct {
@@ -114,7 +117,8 @@ typedef struct fiedler_plan fiedler_plan;
 /* Fills opts with the defaults: FP32_FP64RED, coarse_max_n 25, max_levels 30,
  * stall_ratio 0.9, gs_sweeps 2, pi_max_iters 10000, pi_max_iters_coarsest
  * 100000, pi_cos_tol 1e-6, resid_tol 0, hashed ties, seed 20160214,
- * validate 1, tail_max_n 4096, barrier_timeout_ms 5000, fault_inject 0. */
+ * validate 1, tail_max_n 4096, barrier_timeout_ms 5000, fault_inject 0,
+ * hbm_budget_bytes 0 (16 GiB), max_batch 1024, max_inflight 2. */
 void fiedler_options_default(fiedler_options *opts);
 
 /* Creates a plan on the current CUDA device.  opts may be NULL (defaults);
@@ -131,9 +135,23 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
  * EDEGENERATE; ENOTCONVERGED still fills the result. */
 fiedler_status fiedler_solve(fiedler_plan *plan, const fiedler_graph *graph, fiedler_result *result);
 
-/* Asynchronous form: copies the graph (host or device) into plan-owned memory,
- * queues the solve and returns a ticket at once.  Thread-safe against
- * fiedler_poll and fiedler_cancel on the same plan. */
+/* Batched form: solves `count` independent graphs in one persistent launch
+ * (each graph by one thread block running every level of its hierarchy;
+ * blocks take the next graph when they finish one).  results[i] is filled as
+ * by fiedler_solve (results[i].x / x_on_device give the output buffer, may be
+ * NULL); a graph's result does not depend on the other graphs of the batch.
+ * Returns FIEDLER_OK if the batch ran (per-graph outcomes in results[i].status),
+ * or the error that stopped it. */
+fiedler_status fiedler_solve_batch(fiedler_plan *plan, const fiedler_graph *graphs, int count,
+                                   fiedler_result *results);
+
+/* Serving form (continuous batching): fiedler_batch_submit copies the graph
+ * (host or device) into plan-owned memory, queues it and returns a ticket at
+ * once.  A scheduler thread admits queued tickets into batched launches while
+ * the device memory held by in-flight tickets stays within hbm_budget_bytes;
+ * up to max_inflight launches run concurrently on their own streams, so
+ * tickets that arrive while others are on the GPU start as soon as memory and
+ * a launch slot free up.  Thread-safe against fiedler_poll / fiedler_cancel. */
 fiedler_status fiedler_batch_submit(fiedler_plan *plan, const fiedler_graph *graph, uint64_t *ticket);
 
 /* Waits up to timeout_ms (0 = do not wait, < 0 = wait forever) for a ticket.
@@ -195,6 +213,16 @@ typedef struct {
   double phase_ms[2][16];    /* device-timer time per phase, [0] grid-wide kernel, [1] one-block kernel */
   double phase_bytes[2][16]; /* algorithmic bytes per phase, same split */
 } fiedler_profile;
+
+typedef struct {
+  uint64_t submitted, completed, batches;  /* serving counters since plan creation */
+  double p50_ms, p99_ms, mean_ms;           /* ticket latency, submit to completion */
+  double mean_batch;                        /* tickets per batched launch */
+  size_t peak_inflight_bytes;               /* most device memory held by in-flight tickets */
+} fiedler_serving_stats;
+
+/* Counters of the serving form. */
+fiedler_status fiedler_plan_serving_stats(const fiedler_plan *plan, fiedler_serving_stats *out);
 
 /* 1: record CUDA events around every kernel of the following solves. */
 fiedler_status fiedler_plan_set_profiling(fiedler_plan *plan, int on);

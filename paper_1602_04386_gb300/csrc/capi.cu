@@ -12,6 +12,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -36,9 +37,47 @@ struct Ticket {
   void *w = nullptr;
   int w_dtype = 0;
   double *x = nullptr;  // device result vector
+  size_t footprint = 0;  // device bytes while in flight (admission)
+  std::chrono::steady_clock::time_point t_submit;
   fiedler_result res{};
   fiedler_status st = FIEDLER_EAGAIN;
   bool done = false, canceled = false, running = false;
+};
+
+// One graph of a batched launch.
+struct BatchItem {
+  int64_t n, nnz;
+  const int32_t *rp, *ci;
+  const void *w;
+  int wf64;
+  bool host_in;          // inputs are host pointers: packed into the staging region
+  double *user_x;        // caller's output (may be NULL)
+  int user_x_dev;
+  size_t arena_b, scratch_b;
+  size_t in_off, x_off;  // offsets in the input / output staging regions
+  fiedler_result *res;   // where the result goes (solve_batch) or NULL (ticket)
+  Ticket *ticket;
+  int st;                // internal status after the run
+};
+
+// A batched launch in preparation or in flight: own stream, device buffer,
+// pinned staging, completion event.
+struct BatchCtx {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t done = nullptr;
+  char *d_buf = nullptr;
+  size_t d_cap = 0;
+  char *h_buf = nullptr;  // pinned
+  size_t h_cap = 0;
+  std::vector<BatchItem> items;
+  size_t footprint = 0;
+  bool busy = false;
+  int type = 1;
+  // layout (offsets in d_buf / h_buf)
+  size_t d_states, d_counter, d_scratch, slot_bytes, d_arena, d_in, d_x, d_total;
+  size_t h_states, h_in, h_x, h_total, in_bytes, x_bytes;
+  int nslots = 0;
 };
 
 }  // namespace
@@ -50,6 +89,7 @@ struct fiedler_plan {
   int device = 0, sms = 0;
   fz::KernelSet ks[2];      // [0] double, [1] float
   int grid_blocks[2][2];    // [type][setup/solve]
+  int batch_slots[2];       // resident blocks of the batched kernel
   State *d_state = nullptr;
   State *h_state = nullptr; // pinned mirror
   fz::IRed *d_ipart = nullptr;
@@ -67,7 +107,9 @@ struct fiedler_plan {
   int last_type = 1;
   bool have_result = false;
   fiedler_profile prof;
-  // batch form
+  BatchCtx bsync;           // fiedler_solve_batch (plan stream)
+  BatchCtx bserve[4];       // serving launches (own streams)
+  // serving form
   std::mutex exec_mu;       // one solve on the device state at a time
   std::mutex q_mu;
   std::condition_variable q_cv;
@@ -76,6 +118,9 @@ struct fiedler_plan {
   uint64_t next_ticket = 1;
   std::thread worker;
   bool stop = false;
+  size_t inflight_bytes = 0, peak_inflight = 0;
+  uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, n_batched_tickets = 0;
+  std::vector<float> latencies_ms;
 };
 
 namespace {
@@ -141,6 +186,27 @@ fiedler_status map_status(int st) {
   }
 }
 
+void fill_opts(fz::Opts &o, const fiedler_options &u, int type) {
+  o.precision = u.precision;
+  o.coarse_max_n = u.coarse_max_n;
+  o.max_levels = u.max_levels;
+  o.gs_sweeps = u.gs_sweeps;
+  o.pi_max_iters = u.pi_max_iters;
+  o.pi_max_iters_coarsest = u.pi_max_iters_coarsest;
+  o.tie_rule = u.tie_rule;
+  o.validate = u.validate;
+  o.tail_max_n = u.tail_max_n;
+  o.fault_inject = u.fault_inject;
+  o.stall_ratio = u.stall_ratio;
+  o.pi_cos_tol = u.pi_cos_tol;
+  o.resid_tol = u.resid_tol;
+  // annihilation guard on the deflated norm of a unit vector: above the
+  // rounding noise of the fused variance sum x^2 - (sum x)^2 / n
+  o.guard = type == 0 ? ldexp(1.0, -20) : ldexp(1.0, -16);
+  o.seed = u.seed;
+  o.barrier_timeout_ns = (unsigned long long)u.barrier_timeout_ms * 1000000ull;
+}
+
 const char *kPhaseNames[fz::PH_COUNT] = {"ingest", "colour", "reorder", "match", "aggregate", "galerkin",
                                          "coarsest", "prolong", "gauss_seidel", "power_iter", "final"};
 
@@ -171,25 +237,7 @@ fiedler_status run_solve(fiedler_plan *p, int64_t n, int64_t nnz, const int32_t 
     if ((st = ensure(p, (void **)&p->d_scratch, &p->scratch_cap, sbytes)) != FIEDLER_OK) return st;
     State *h = p->h_state;
     memset(h, 0, sizeof(State));
-    fz::Opts &o = h->opt;
-    o.precision = p->opt.precision;
-    o.coarse_max_n = p->opt.coarse_max_n;
-    o.max_levels = p->opt.max_levels;
-    o.gs_sweeps = p->opt.gs_sweeps;
-    o.pi_max_iters = p->opt.pi_max_iters;
-    o.pi_max_iters_coarsest = p->opt.pi_max_iters_coarsest;
-    o.tie_rule = p->opt.tie_rule;
-    o.validate = p->opt.validate;
-    o.tail_max_n = p->opt.tail_max_n;
-    o.fault_inject = p->opt.fault_inject;
-    o.stall_ratio = p->opt.stall_ratio;
-    o.pi_cos_tol = p->opt.pi_cos_tol;
-    o.resid_tol = p->opt.resid_tol;
-    // annihilation guard on the deflated norm of a unit vector: above the
-    // rounding noise of the fused variance sum x^2 - (sum x)^2 / n
-    o.guard = type == 0 ? ldexp(1.0, -20) : ldexp(1.0, -16);
-    o.seed = p->opt.seed;
-    o.barrier_timeout_ns = (unsigned long long)p->opt.barrier_timeout_ms * 1000000ull;
+    fill_opts(h->opt, p->opt, type);
     h->bad_index = LLONG_MAX;
     h->n0 = (int)n;
     h->nnz0 = (int)nnz;
@@ -329,52 +377,329 @@ fiedler_status solve_locked(fiedler_plan *p, const fiedler_graph *g, fiedler_res
   return st;
 }
 
-// ---- batch form: a worker thread drains the ticket queue -------------------
-void worker_main(fiedler_plan *p) {
-  cudaSetDevice(p->device);
-  for (;;) {
-    Ticket *t = nullptr;
-    {
-      std::unique_lock<std::mutex> lk(p->q_mu);
-      p->q_cv.wait(lk, [&] { return p->stop || !p->queue.empty(); });
-      if (p->stop) return;
-      uint64_t id = p->queue.front();
-      p->queue.pop_front();
-      auto it = p->tickets.find(id);
-      if (it == p->tickets.end()) continue;
-      t = it->second;
-      if (t->canceled) {
-        t->st = FIEDLER_ECANCELED;
-        t->done = true;
-        p->q_cv.notify_all();
-        continue;
+// ---- batched form --------------------------------------------------------
+size_t r256(size_t b) { return (b + 255u) & ~(size_t)255u; }
+
+fiedler_status ctx_reserve(BatchCtx &c, size_t dbytes, size_t hbytes) {
+  if (c.d_cap < dbytes) {
+    if (c.d_buf) CK(cudaFreeAsync(c.d_buf, c.stream));
+    c.d_buf = nullptr;
+    c.d_cap = 0;
+    CK(cudaMallocAsync((void **)&c.d_buf, dbytes, c.stream));
+    c.d_cap = dbytes;
+  }
+  if (c.h_cap < hbytes) {
+    if (c.h_buf) {
+      CK(cudaStreamSynchronize(c.stream));
+      cudaFreeHost(c.h_buf);
+    }
+    c.h_buf = nullptr;
+    c.h_cap = 0;
+    CK(cudaMallocHost((void **)&c.h_buf, hbytes));
+    c.h_cap = hbytes;
+  }
+  return FIEDLER_OK;
+}
+
+// device bytes one graph holds while its batch is in flight (admission)
+size_t item_footprint(int64_t n, int64_t nnz, size_t tsz, bool wf64) {
+  return r256(sizeof(State)) + r256(arena_estimate(n, nnz, tsz, wf64)) + r256(scratch_estimate(n, nnz, 1));
+}
+
+// Lays out and queues one batched launch of c.items on c.stream (asynchronous).
+// The items are ordered by decreasing size so the largest graphs start first.
+fiedler_status batch_launch(fiedler_plan *p, BatchCtx &c, double arena_scale) {
+  const int type = c.type;
+  const size_t tsz = type == 0 ? 8 : 4;
+  std::stable_sort(c.items.begin(), c.items.end(),
+                   [](const BatchItem &a, const BatchItem &b) { return a.nnz + a.n > b.nnz + b.n; });
+  const int count = (int)c.items.size();
+  const int nslots = std::min(count, p->batch_slots[type]);
+  size_t slot = 0, arenas = 0, in_b = 0, x_b = 0;
+  for (auto &it : c.items) {
+    it.arena_b = r256((size_t)(arena_estimate(it.n, it.nnz, tsz, it.wf64) * arena_scale));
+    it.scratch_b = r256((size_t)(scratch_estimate(it.n, it.nnz, 1) * arena_scale));
+    slot = std::max(slot, it.scratch_b);
+    arenas += it.arena_b;
+    if (it.host_in) {
+      it.in_off = in_b;
+      in_b += r256(4 * (size_t)(it.n + 1)) + r256(4 * (size_t)std::max<int64_t>(it.nnz, 1)) +
+              r256((it.wf64 ? 8 : 4) * (size_t)std::max<int64_t>(it.nnz, 1));
+    }
+    if (it.user_x && !it.user_x_dev) {
+      it.x_off = x_b;
+      x_b += r256(8 * (size_t)it.n);
+    }
+  }
+  const size_t states_b = r256(sizeof(State) * (size_t)count);
+  c.nslots = nslots;
+  c.slot_bytes = slot;
+  c.d_states = 0;
+  c.d_counter = states_b;
+  c.d_scratch = c.d_counter + 256;
+  c.d_arena = c.d_scratch + slot * (size_t)nslots;
+  c.d_in = c.d_arena + arenas;
+  c.d_x = c.d_in + in_b;
+  c.d_total = c.d_x + x_b;
+  c.h_states = 0;
+  c.h_in = states_b;
+  c.h_x = c.h_in + in_b;
+  c.h_total = c.h_x + x_b;
+  c.in_bytes = in_b;
+  c.x_bytes = x_b;
+  fiedler_status st = ctx_reserve(c, c.d_total, c.h_total);
+  if (st != FIEDLER_OK) return st;
+  // host-side state of every graph, packed inputs
+  State *hs = (State *)(c.h_buf + c.h_states);
+  size_t aoff = c.d_arena;
+  for (int i = 0; i < count; i++) {
+    BatchItem &it = c.items[i];
+    State *h = hs + i;
+    memset(h, 0, sizeof(State));
+    fill_opts(h->opt, p->opt, type);
+    h->opt.tail_max_n = INT_MAX;  // every level in the one-block engine
+    h->opt.fault_inject = 0;
+    h->bad_index = LLONG_MAX;
+    h->n0 = (int)it.n;
+    h->nnz0 = (int)it.nnz;
+    if (it.host_in) {
+      char *hin = c.h_buf + c.h_in + it.in_off;
+      char *din = c.d_buf + c.d_in + it.in_off;
+      const size_t rb = r256(4 * (size_t)(it.n + 1)), cb = r256(4 * (size_t)std::max<int64_t>(it.nnz, 1));
+      memcpy(hin, it.rp, 4 * (size_t)(it.n + 1));
+      if (it.nnz > 0) {
+        memcpy(hin + rb, it.ci, 4 * (size_t)it.nnz);
+        memcpy(hin + rb + cb, it.w, (it.wf64 ? 8 : 4) * (size_t)it.nnz);
       }
-      t->running = true;
+      h->in_rowptr = (const int *)din;
+      h->in_col = (const int *)(din + rb);
+      h->in_w = din + rb + cb;
+    } else {
+      h->in_rowptr = it.rp;
+      h->in_col = it.ci;
+      h->in_w = it.w;
     }
-    fiedler_graph g{t->n, t->nnz, t->rowptr, t->col, t->w, t->w_dtype, 1};
+    h->in_w_f64 = it.wf64;
+    h->arena = c.d_buf + aoff;
+    h->arena_size = it.arena_b;
+    aoff += it.arena_b;
+    h->xout = it.user_x ? (it.user_x_dev ? it.user_x : (double *)(c.d_buf + c.d_x + it.x_off)) : nullptr;
+  }
+  if (in_b) CK(cudaMemcpyAsync(c.d_buf + c.d_in, c.h_buf + c.h_in, in_b, cudaMemcpyHostToDevice, c.stream));
+  CK(cudaMemcpyAsync(c.d_buf + c.d_states, hs, sizeof(State) * (size_t)count, cudaMemcpyHostToDevice, c.stream));
+  CK(cudaMemsetAsync(c.d_buf + c.d_counter, 0, 4, c.stream));
+  State *d_states = (State *)(c.d_buf + c.d_states);
+  int *d_counter = (int *)(c.d_buf + c.d_counter);
+  char *d_scratch = c.d_buf + c.d_scratch;
+  unsigned long long slot_bytes = c.slot_bytes;
+  void *args[] = {(void *)&d_states, (void *)&count, (void *)&d_counter, (void *)&d_scratch, (void *)&slot_bytes};
+  CK(cudaLaunchKernel(p->ks[type].batch, dim3(nslots), dim3(fz::kCtaThreads), args, 0, c.stream));
+  CK(cudaMemcpyAsync(hs, c.d_buf + c.d_states, sizeof(State) * (size_t)count, cudaMemcpyDeviceToHost, c.stream));
+  if (x_b) CK(cudaMemcpyAsync(c.h_buf + c.h_x, c.d_buf + c.d_x, x_b, cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaEventRecord(c.done, c.stream));
+  return FIEDLER_OK;
+}
+
+// Reads back one finished launch; results of items whose hierarchy outgrew
+// its arena are left with st = ST_ARENA / ST_SCRATCH for a rerun.
+void batch_collect(BatchCtx &c) {
+  State *hs = (State *)(c.h_buf + c.h_states);
+  for (size_t i = 0; i < c.items.size(); i++) {
+    BatchItem &it = c.items[i];
+    const State *h = hs + i;
+    it.st = h->status;
     fiedler_result r{};
-    r.x = t->x;
-    r.x_on_device = 1;
-    fiedler_status st;
-    {
-      std::lock_guard<std::mutex> ex(p->exec_mu);
-      st = solve_locked(p, &g, &r);
+    fiedler_status out = map_status(h->status);
+    if (out == FIEDLER_OK && !h->finalized) out = FIEDLER_ECUDA;
+    if (out == FIEDLER_OK && h->capped) out = FIEDLER_ENOTCONVERGED;
+    r.levels = h->nlevels;
+    r.coarsest_n = h->nlevels > 0 ? h->lv[h->coarsest].n : 0;
+    r.bad_index = h->bad_index == LLONG_MAX ? -1 : h->bad_index;
+    if (out == FIEDLER_OK || out == FIEDLER_ENOTCONVERGED) {
+      r.lambda2 = h->lambda;
+      r.residual = h->residual;
+      r.ortho = h->ortho;
+      r.pi_iters_total = h->pi_total;
+      r.gs_sweeps_total = h->gs_total;
+      if (it.user_x && !it.user_x_dev) memcpy(it.user_x, c.h_buf + c.h_x + it.x_off, 8 * (size_t)it.n);
     }
-    std::lock_guard<std::mutex> lk(p->q_mu);
-    t->res = r;
-    t->st = st;
-    t->done = true;
-    t->running = false;
-    p->q_cv.notify_all();
+    r.x = it.user_x;
+    r.x_on_device = it.user_x_dev;
+    r.status = out;
+    if (it.res) *it.res = r;
+    if (it.ticket) {
+      it.ticket->res = r;
+      it.ticket->st = out;
+    }
   }
 }
 
-void free_ticket(fiedler_plan *p, Ticket *t) {
+bool needs_rerun(int st) { return st == fz::ST_ARENA || st == fz::ST_SCRATCH; }
+
+// Runs c.items to completion on c.stream, growing arenas for graphs whose
+// hierarchy outgrew the first estimate (their rerun uses the same engine).
+fiedler_status batch_run_sync(fiedler_plan *p, BatchCtx &c) {
+  double scale = 1.0;
+  std::vector<BatchItem> all = c.items;
+  std::vector<BatchItem> todo = c.items;
+  for (int attempt = 0; attempt < 4 && !todo.empty(); attempt++) {
+    c.items = todo;
+    fiedler_status st = batch_launch(p, c, scale);
+    if (st != FIEDLER_OK) return st;
+    CK(cudaEventSynchronize(c.done));
+    batch_collect(c);
+    todo.clear();
+    for (auto &it : c.items)
+      if (needs_rerun(it.st)) todo.push_back(it);
+    scale *= 2.0;
+  }
+  for (auto &it : todo) {
+    if (it.res) it.res->status = FIEDLER_ENOMEM;
+    if (it.ticket) it.ticket->st = FIEDLER_ENOMEM;
+  }
+  c.items = all;
+  return FIEDLER_OK;
+}
+
+void free_ticket(Ticket *t) {
   cudaFree(t->rowptr);
   cudaFree(t->col);
   cudaFree(t->w);
   cudaFree(t->x);
   delete t;
+}
+
+// ---- serving form: continuous batching -----------------------------------
+// The scheduler admits queued tickets into a batched launch while the device
+// memory of in-flight tickets stays within the budget (a launch always takes
+// at least one ticket when nothing else is in flight), keeps up to
+// max_inflight launches running on their own streams, and completes tickets
+// as their launch's event fires.
+void complete_ctx(fiedler_plan *p, BatchCtx &c) {
+  batch_collect(c);
+  std::vector<BatchItem> rerun;
+  for (auto &it : c.items)
+    if (needs_rerun(it.st)) rerun.push_back(it);
+  if (!rerun.empty()) {  // rare: regrow and run those again, synchronously
+    std::vector<BatchItem> keep = c.items;
+    c.items = rerun;
+    double scale = 2.0;
+    for (int attempt = 0; attempt < 3 && !c.items.empty(); attempt++, scale *= 2.0) {
+      if (batch_launch(p, c, scale) != FIEDLER_OK || cudaEventSynchronize(c.done) != cudaSuccess) break;
+      batch_collect(c);
+      std::vector<BatchItem> again;
+      for (auto &it : c.items)
+        if (needs_rerun(it.st)) again.push_back(it);
+      c.items = again;
+    }
+    for (auto &it : c.items) it.ticket->st = FIEDLER_ENOMEM;
+    c.items = keep;
+  }
+  const auto now = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> lk(p->q_mu);
+  for (auto &it : c.items) {
+    Ticket *t = it.ticket;
+    t->done = true;
+    t->running = false;
+    p->inflight_bytes -= t->footprint;
+    p->n_completed++;
+    p->latencies_ms.push_back(std::chrono::duration<float, std::milli>(now - t->t_submit).count());
+  }
+  c.items.clear();
+  c.busy = false;
+  p->q_cv.notify_all();
+}
+
+void worker_main(fiedler_plan *p) {
+  cudaSetDevice(p->device);
+  const int type = p->opt.precision == FIEDLER_FP64 ? 0 : 1;
+  const int nctx = std::max(1, std::min(4, p->opt.max_inflight));
+  const size_t budget = p->opt.hbm_budget_bytes ? p->opt.hbm_budget_bytes : (size_t)16 << 30;
+  const int max_batch = std::max(1, p->opt.max_batch);
+  for (;;) {
+    bool progressed = false;
+    // finished launches
+    for (int k = 0; k < nctx; k++) {
+      BatchCtx &c = p->bserve[k];
+      if (c.busy && cudaEventQuery(c.done) == cudaSuccess) {
+        complete_ctx(p, c);
+        progressed = true;
+      }
+    }
+    // admit a new launch
+    BatchCtx *free_ctx = nullptr;
+    for (int k = 0; k < nctx && !free_ctx; k++)
+      if (!p->bserve[k].busy) free_ctx = &p->bserve[k];
+    {
+      std::unique_lock<std::mutex> lk(p->q_mu);
+      if (p->stop) return;
+      if (free_ctx && !p->queue.empty()) {
+        BatchCtx &c = *free_ctx;
+        c.items.clear();
+        c.type = type;
+        bool any_inflight = p->inflight_bytes > 0;
+        while (!p->queue.empty() && (int)c.items.size() < max_batch) {
+          auto itk = p->tickets.find(p->queue.front());
+          if (itk == p->tickets.end()) {
+            p->queue.pop_front();
+            continue;
+          }
+          Ticket *t = itk->second;
+          if (t->canceled) {
+            p->queue.pop_front();
+            t->st = FIEDLER_ECANCELED;
+            t->done = true;
+            p->q_cv.notify_all();
+            continue;
+          }
+          const bool fits = p->inflight_bytes + t->footprint <= budget;
+          if (!fits && (any_inflight || !c.items.empty())) break;  // wait for memory to free up
+          p->queue.pop_front();
+          t->running = true;
+          p->inflight_bytes += t->footprint;
+          p->peak_inflight = std::max(p->peak_inflight, p->inflight_bytes);
+          BatchItem it{};
+          it.n = t->n;
+          it.nnz = t->nnz;
+          it.rp = t->rowptr;
+          it.ci = t->col;
+          it.w = t->w;
+          it.wf64 = t->w_dtype == FIEDLER_W_F64;
+          it.host_in = false;
+          it.user_x = t->x;
+          it.user_x_dev = 1;
+          it.ticket = t;
+          c.items.push_back(it);
+        }
+        if (!c.items.empty()) {
+          p->n_batches++;
+          p->n_batched_tickets += c.items.size();
+          c.busy = true;
+          lk.unlock();
+          if (batch_launch(p, c, 1.0) != FIEDLER_OK) {
+            std::lock_guard<std::mutex> lk2(p->q_mu);
+            for (auto &it : c.items) {
+              it.ticket->st = FIEDLER_ECUDA;
+              it.ticket->done = true;
+              it.ticket->running = false;
+              p->inflight_bytes -= it.ticket->footprint;
+            }
+            c.items.clear();
+            c.busy = false;
+            p->q_cv.notify_all();
+          }
+          progressed = true;
+          continue;
+        }
+      }
+      bool any_busy = false;
+      for (int k = 0; k < nctx; k++) any_busy |= p->bserve[k].busy;
+      if (!progressed) {
+        if (any_busy) p->q_cv.wait_for(lk, std::chrono::microseconds(50));
+        else p->q_cv.wait(lk, [&] { return p->stop || !p->queue.empty(); });
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -399,6 +724,9 @@ void fiedler_options_default(fiedler_options *o) {
   o->tail_max_n = 4096;
   o->barrier_timeout_ms = 5000;
   o->fault_inject = 0;
+  o->hbm_budget_bytes = 0;
+  o->max_batch = 1024;
+  o->max_inflight = 2;
 }
 
 fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_stream, fiedler_plan **out) {
@@ -411,7 +739,7 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
       o.max_levels < 1 || o.max_levels > fz::kMaxLevels || !(o.stall_ratio > 0.0 && o.stall_ratio <= 1.0) ||
       o.gs_sweeps < 0 || o.pi_max_iters < 0 || o.pi_max_iters_coarsest < 0 || !(o.pi_cos_tol >= 0.0) ||
       !(o.resid_tol >= 0.0) || (o.tie_rule != 0 && o.tie_rule != 1) || o.tail_max_n < 1 ||
-      o.barrier_timeout_ms < 1)
+      o.barrier_timeout_ms < 1 || o.max_batch < 1 || o.max_inflight < 1 || o.max_inflight > 4)
     return FIEDLER_EINVAL;
   fiedler_plan *p = new (std::nothrow) fiedler_plan();
   if (!p) return FIEDLER_ENOMEM;
@@ -441,6 +769,21 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
       int g = bps * p->sms;
       p->grid_blocks[t][k] = g > fz::kMaxBlocks ? fz::kMaxBlocks : g;
     }
+  }
+  for (int t = 0; t < 2; t++) {
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->ks[t].batch, fz::kCtaThreads, 0) != cudaSuccess ||
+        bps < 1)
+      return fail(FIEDLER_ECUDA);
+    p->batch_slots[t] = bps * p->sms;
+  }
+  p->bsync.stream = p->stream;
+  if (cudaEventCreateWithFlags(&p->bsync.done, cudaEventDisableTiming) != cudaSuccess) return fail(FIEDLER_ECUDA);
+  for (int k = 0; k < 4; k++) {
+    BatchCtx &c = p->bserve[k];
+    if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FIEDLER_ECUDA);
+    c.own_stream = true;
+    if (cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) return fail(FIEDLER_ECUDA);
   }
   if (cudaMalloc(&p->d_state, sizeof(State)) != cudaSuccess) return fail(FIEDLER_ENOMEM);
   if (cudaMalloc(&p->d_ipart, sizeof(fz::IRed) * 2 * fz::kMaxBlocks) != cudaSuccess) return fail(FIEDLER_ENOMEM);
@@ -483,15 +826,74 @@ fiedler_status fiedler_batch_submit(fiedler_plan *p, const fiedler_graph *g, uin
   if (e == cudaSuccess && g->nnz > 0) e = cudaMemcpy(t->col, g->col, 4 * (size_t)g->nnz, kind);
   if (e == cudaSuccess && g->nnz > 0) e = cudaMemcpy(t->w, g->w, wsz * (size_t)g->nnz, kind);
   if (e != cudaSuccess) {
-    free_ticket(p, t);
+    free_ticket(t);
     return map_cuda(e);
   }
+  t->footprint = item_footprint(g->n, g->nnz, p->opt.precision == FIEDLER_FP64 ? 8 : 4, g->w_dtype == FIEDLER_W_F64);
+  t->t_submit = std::chrono::steady_clock::now();
   std::lock_guard<std::mutex> lk(p->q_mu);
   t->id = p->next_ticket++;
   p->tickets[t->id] = t;
   p->queue.push_back(t->id);
+  p->n_submitted++;
   *ticket = t->id;
   p->q_cv.notify_all();
+  return FIEDLER_OK;
+}
+
+fiedler_status fiedler_solve_batch(fiedler_plan *p, const fiedler_graph *graphs, int count, fiedler_result *results) {
+  if (!p || count < 0 || (count > 0 && (!graphs || !results))) return FIEDLER_EINVAL;
+  std::lock_guard<std::mutex> ex(p->exec_mu);
+  BatchCtx &c = p->bsync;
+  c.items.clear();
+  c.type = p->opt.precision == FIEDLER_FP64 ? 0 : 1;
+  for (int i = 0; i < count; i++) {
+    const fiedler_graph &g = graphs[i];
+    fiedler_result &r = results[i];
+    double *ux = r.x;
+    const int uxd = r.x_on_device;
+    fiedler_status st = check_graph(&g, &r);
+    if (st != FIEDLER_OK) {
+      r.status = st;
+      continue;
+    }
+    BatchItem it{};
+    it.n = g.n;
+    it.nnz = g.nnz;
+    it.rp = g.rowptr;
+    it.ci = g.col;
+    it.w = g.w;
+    it.wf64 = g.w_dtype == FIEDLER_W_F64;
+    it.host_in = !g.on_device;
+    it.user_x = ux;
+    it.user_x_dev = uxd;
+    it.res = &r;
+    c.items.push_back(it);
+  }
+  if (c.items.empty()) return FIEDLER_OK;
+  return batch_run_sync(p, c);
+}
+
+fiedler_status fiedler_plan_serving_stats(const fiedler_plan *cp, fiedler_serving_stats *out) {
+  if (!cp || !out) return FIEDLER_EINVAL;
+  fiedler_plan *p = const_cast<fiedler_plan *>(cp);
+  std::lock_guard<std::mutex> lk(p->q_mu);
+  memset(out, 0, sizeof(*out));
+  out->submitted = p->n_submitted;
+  out->completed = p->n_completed;
+  out->batches = p->n_batches;
+  out->mean_batch = p->n_batches ? (double)p->n_batched_tickets / (double)p->n_batches : 0.0;
+  out->peak_inflight_bytes = p->peak_inflight;
+  if (!p->latencies_ms.empty()) {
+    std::vector<float> v = p->latencies_ms;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double q) { return (double)v[std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5))]; };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    double sum = 0.0;
+    for (float x : v) sum += x;
+    out->mean_ms = sum / (double)v.size();
+  }
   return FIEDLER_OK;
 }
 
@@ -521,7 +923,7 @@ fiedler_status fiedler_poll(fiedler_plan *p, uint64_t ticket, int timeout_ms, fi
     }
   }
   p->tickets.erase(it);
-  free_ticket(p, t);
+  free_ticket(t);
   return st;
 }
 
@@ -543,8 +945,18 @@ void fiedler_plan_destroy(fiedler_plan *p) {
     p->q_cv.notify_all();
   }
   if (p->worker.joinable()) p->worker.join();
-  for (auto &kv : p->tickets) free_ticket(p, kv.second);
+  for (int k = 0; k < 4; k++)
+    if (p->bserve[k].stream) cudaStreamSynchronize(p->bserve[k].stream);
+  for (auto &kv : p->tickets) free_ticket(kv.second);
   p->tickets.clear();
+  BatchCtx *ctxs[5] = {&p->bsync, &p->bserve[0], &p->bserve[1], &p->bserve[2], &p->bserve[3]};
+  for (BatchCtx *c : ctxs) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->d_buf) cudaFree(c->d_buf);
+    if (c->h_buf) cudaFreeHost(c->h_buf);
+    if (c->done) cudaEventDestroy(c->done);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  }
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->d_arena) cudaFreeAsync(p->d_arena, p->stream);
   if (p->d_scratch) cudaFreeAsync(p->d_scratch, p->stream);

@@ -341,10 +341,12 @@ struct Eng {
   // ---- infrastructure ------------------------------------------------------
   FZD void init(State *s) {
     S = s;
-    bid = blockIdx.x;
-    nb = gridDim.x;
-    tid = blockIdx.x * blockDim.x + threadIdx.x;
-    nthr = gridDim.x * blockDim.x;
+    // the one-block form treats its block as the whole grid, whichever block
+    // of a batched launch it is
+    bid = GRID ? blockIdx.x : 0;
+    nb = GRID ? gridDim.x : 1;
+    tid = GRID ? blockIdx.x * blockDim.x + threadIdx.x : threadIdx.x;
+    nthr = GRID ? gridDim.x * blockDim.x : blockDim.x;
     rb = 0;
     kind = GRID ? 0 : 1;
     aoff = S->arena_off;
@@ -1973,6 +1975,30 @@ FZD void engine_entry(State *S, int mode) {
   E.run(mode);
   E.persist();
   E.flush_profile();
+}
+
+// Batched form: persistent blocks pull graph indices from a device counter
+// and run the one-block engine on each graph's own state, with the block's
+// private scratch slot.  A graph's computation does not depend on which block
+// runs it or on the other graphs of the batch.
+template <class T>
+FZD void batch_entry(State *states, int count, int *next, char *scratch, unsigned long long slot_bytes) {
+  __shared__ int s_g;
+  for (;;) {
+    if (threadIdx.x == 0) s_g = atomicAdd(next, 1);
+    __syncthreads();
+    const int g = s_g;
+    __syncthreads();
+    if (g >= count) return;
+    State *S = states + g;
+    if (threadIdx.x == 0) {
+      S->scratch = scratch + (size_t)blockIdx.x * slot_bytes;
+      S->scratch_size = slot_bytes;
+    }
+    __syncthreads();
+    engine_entry<T, false>(S, 1);
+    __syncthreads();
+  }
 }
 
 }  // namespace fz

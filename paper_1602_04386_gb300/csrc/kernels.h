@@ -7,6 +7,7 @@ struct KernelSet {
   const void *grid_setup;  // cooperative, kGridThreads per block: setup of levels with n > tail_max_n
   const void *grid_solve;  // cooperative, kGridThreads per block: solve of levels with n > tail_max_n
   const void *cta;         // one block of kCtaThreads: everything on levels with n <= tail_max_n
+  const void *batch;       // persistent blocks of kCtaThreads, one graph at a time each
   const char *names[3];    // in launch order: grid_setup, cta, grid_solve
 };
 void kernels_f32(KernelSet *k);

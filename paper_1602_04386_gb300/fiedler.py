@@ -44,6 +44,7 @@ SYMBOLS = (
     "fiedler_poll", "fiedler_cancel", "fiedler_plan_destroy", "fiedler_status_str",
     "fiedler_plan_num_levels", "fiedler_plan_level_info", "fiedler_plan_copy_level",
     "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc",
+    "fiedler_solve_batch", "fiedler_plan_serving_stats",
 )
 
 
@@ -64,6 +65,9 @@ class fiedler_options(C.Structure):
         ("tail_max_n", C.c_int),
         ("barrier_timeout_ms", C.c_int),
         ("fault_inject", C.c_int),
+        ("hbm_budget_bytes", C.c_size_t),
+        ("max_batch", C.c_int),
+        ("max_inflight", C.c_int),
     ]
 
 
@@ -109,6 +113,19 @@ class fiedler_level_info(C.Structure):
         ("sigma", C.c_double),
         ("last_cos", C.c_double),
         ("phase_ms", C.c_float * 16),
+    ]
+
+
+class fiedler_serving_stats(C.Structure):
+    _fields_ = [
+        ("submitted", C.c_uint64),
+        ("completed", C.c_uint64),
+        ("batches", C.c_uint64),
+        ("p50_ms", C.c_double),
+        ("p99_ms", C.c_double),
+        ("mean_ms", C.c_double),
+        ("mean_batch", C.c_double),
+        ("peak_inflight_bytes", C.c_size_t),
     ]
 
 
@@ -165,9 +182,12 @@ def load():
         L.fiedler_plan_get_profile.argtypes = [vp, C.POINTER(fiedler_profile)]
         L.fiedler_solve_noalloc.argtypes = [C.POINTER(fiedler_options), C.POINTER(fiedler_graph), vp, vp,
                                             C.POINTER(fiedler_result)]
+        L.fiedler_solve_batch.argtypes = [vp, C.POINTER(fiedler_graph), C.c_int, C.POINTER(fiedler_result)]
+        L.fiedler_plan_serving_stats.argtypes = [vp, C.POINTER(fiedler_serving_stats)]
         for f in ("fiedler_plan_create", "fiedler_solve", "fiedler_batch_submit", "fiedler_poll", "fiedler_cancel",
                   "fiedler_plan_num_levels", "fiedler_plan_level_info", "fiedler_plan_copy_level",
-                  "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc"):
+                  "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc",
+                  "fiedler_solve_batch", "fiedler_plan_serving_stats"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -236,6 +256,17 @@ def fiedler_plan_get_profile(plan):
     pr = fiedler_profile()
     st = load().fiedler_plan_get_profile(plan, C.byref(pr))
     return st, pr
+
+
+def fiedler_solve_batch(plan, graphs, results) -> int:
+    """graphs: ctypes array of fiedler_graph; results: ctypes array of fiedler_result."""
+    return load().fiedler_solve_batch(plan, graphs, len(graphs), results)
+
+
+def fiedler_plan_serving_stats(plan):
+    out = fiedler_serving_stats()
+    st = load().fiedler_plan_serving_stats(plan, C.byref(out))
+    return st, out
 
 
 def fiedler_solve_noalloc(opts: fiedler_options | None, graph: fiedler_graph, x_dev_ptr, cuda_stream,
@@ -404,3 +435,28 @@ class Plan:
 
     def cancel(self, ticket) -> int:
         return fiedler_cancel(self.h, ticket)
+
+    def serving_stats(self) -> fiedler_serving_stats:
+        st, out = fiedler_plan_serving_stats(self.h)
+        return out
+
+    def solve_batch(self, graphs, on_device=True, want_x=True):
+        """Batched solve of a list of inputs.CSR; returns a list of Result (x as numpy)."""
+        keep = []
+        garr = (fiedler_graph * len(graphs))()
+        rarr = (fiedler_result * len(graphs))()
+        xs = []
+        for i, g in enumerate(graphs):
+            gs, k = device_graph(g) if on_device else host_graph(g)
+            keep.append(k)
+            garr[i] = gs
+            x = np.zeros(g.n, np.float64) if want_x else None
+            xs.append(x)
+            if x is not None:
+                rarr[i].x = x.ctypes.data
+                rarr[i].x_on_device = 0
+        st = fiedler_solve_batch(self.h, garr, rarr)
+        if st != FIEDLER_OK:
+            raise FiedlerError(st, "fiedler_solve_batch")
+        del keep
+        return [Result(rarr[i], xs[i]) for i in range(len(graphs))]
