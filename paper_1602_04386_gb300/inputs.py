@@ -193,3 +193,92 @@ def with_self_loops(g: CSR, rows, weight=1.0) -> CSR:
         ws += vs
         rp.append(len(cols))
     return CSR(g.n, np.asarray(rp), np.asarray(cols), np.asarray(ws, dtype=g.w.dtype), name=g.name + "+loops")
+
+
+def largest_component(g: CSR) -> CSR:
+    """Induced subgraph on the largest connected component (vertex order kept)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    a = sp.csr_matrix((np.ones(g.nnz), g.col, g.rowptr), shape=(g.n, g.n))
+    k, lab = connected_components(a, directed=False)
+    if k == 1:
+        return g
+    big = np.argmax(np.bincount(lab))
+    keep = np.flatnonzero(lab == big)
+    new = np.full(g.n, -1, np.int64)
+    new[keep] = np.arange(keep.size)
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    m = (new[rows] >= 0) & (new[g.col] >= 0)
+    r, c, w = new[rows[m]], new[g.col[m]], g.w[m]
+    rowptr = np.zeros(keep.size + 1, np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    return CSR(keep.size, np.cumsum(rowptr), c, w, name=g.name + "-lcc")
+
+
+def rmat(scale: int, edge_factor: int = 8, a=0.57, b=0.19, c=0.19, seed: int = BASE_SEED + 4,
+         wlo=0.1, whi=1.0, dtype=np.float32) -> CSR:
+    """R-MAT graph: edge_factor * 2^scale draws, each choosing one quadrant per
+    bit level with probabilities (a, b, c, 1-a-b-c); symmetrised, duplicates and
+    self-loops removed, weights uniform in [wlo, whi) per undirected edge
+    (rounded to f32), largest connected component kept."""
+    n = 1 << scale
+    m = edge_factor * n
+    u = uniform01(seed, np.arange(m * scale, dtype=np.int64)).reshape(m, scale)
+    q = (u >= a).astype(np.int64) + (u >= a + b) + (u >= a + b + c)  # quadrant 0..3
+    rbit = (q >= 2).astype(np.int64)
+    cbit = (q % 2).astype(np.int64)
+    pw = 1 << np.arange(scale - 1, -1, -1, dtype=np.int64)
+    src = rbit @ pw
+    dst = cbit @ pw
+    keep = src != dst
+    lo, hi = np.minimum(src[keep], dst[keep]), np.maximum(src[keep], dst[keep])
+    key = np.unique(lo * n + hi)
+    lo, hi = key // n, key % n
+    w = (wlo + (whi - wlo) * uniform01(seed + 1, np.arange(key.size))).astype(np.float32)
+    g = csr_from_edges(n, lo, hi, w.astype(dtype), dtype=dtype, name=f"rmat{scale}-s{seed}")
+    return largest_component(g)
+
+
+def knn_mixture(npts: int = 200_000, k: int = 10, clusters: int = 8, sigma: float = 0.5, box: float = 10.0,
+                seed: int = BASE_SEED + 3, dtype=np.float32) -> CSR:
+    """Points from a mixture of isotropic Gaussians (point i in component
+    i mod clusters, means uniform in [0, box]^2, Box-Muller normals), exact
+    k-nearest-neighbour graph symmetrised by union, weights exp(-d^2 / 0.25)
+    rounded to f32, largest connected component kept."""
+    from scipy.spatial import cKDTree
+    means = uniform01(seed, np.arange(2 * clusters)).reshape(clusters, 2) * box
+    u1 = uniform01(seed + 1, np.arange(npts))
+    u2 = uniform01(seed + 2, np.arange(npts))
+    u1 = np.maximum(u1, 2.0 ** -53)
+    rad = np.sqrt(-2.0 * np.log(u1))
+    z = np.stack([rad * np.cos(2 * np.pi * u2), rad * np.sin(2 * np.pi * u2)], axis=1)
+    pts = means[np.arange(npts) % clusters] + sigma * z
+    d, idx = cKDTree(pts).query(pts, k=k + 1)
+    src = np.repeat(np.arange(npts, dtype=np.int64), k)
+    dst = idx[:, 1:].ravel().astype(np.int64)
+    dd = d[:, 1:].ravel()
+    keep = src != dst
+    lo, hi, dd = np.minimum(src[keep], dst[keep]), np.maximum(src[keep], dst[keep]), dd[keep]
+    key, first = np.unique(lo * npts + hi, return_index=True)
+    lo, hi, dd = key // npts, key % npts, dd[first]
+    w = np.exp(-dd * dd / 0.25).astype(np.float32)
+    w = np.maximum(w, np.float32(np.finfo(np.float32).tiny))  # keep every weight positive
+    g = csr_from_edges(npts, lo, hi, w.astype(dtype), dtype=dtype, name=f"knn{npts}-s{seed}")
+    return largest_component(g)
+
+
+def batch_mix(count: int = 4096, seed: int = BASE_SEED + 4, scale_range=(9, 16), side_range=(20, 300)):
+    """The batched workload: even ids 2-D grids with sides uniform in
+    side_range and unit weights, odd ids R-MAT graphs with scale uniform in
+    scale_range (edge factor 8, weights uniform [0.1, 1))."""
+    out = []
+    u = uniform01(seed, np.arange(3 * count))
+    for i in range(count):
+        if i % 2 == 0:
+            m = side_range[0] + int(u[3 * i] * (side_range[1] - side_range[0] + 1))
+            k = side_range[0] + int(u[3 * i + 1] * (side_range[1] - side_range[0] + 1))
+            out.append(grid(m, k, "unit"))
+        else:
+            s = scale_range[0] + int(u[3 * i + 2] * (scale_range[1] - scale_range[0] + 1))
+            out.append(rmat(s, seed=seed + 1000 + i))
+    return out

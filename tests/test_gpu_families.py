@@ -1,0 +1,68 @@
+"""Parity on the batched / spectral-clustering workload families: R-MAT
+(skewed degrees: hub rows, large aggregates and segments take the block-level
+sort paths) and the Gaussian-mixture kNN graph (weights exp(-d^2/0.25) span
+many binades, so the FP64 Galerkin sums depend on their order).  Hierarchy
+bit for bit, lambda_2 within 1e-10 (FP64) / 1e-5 (FP32) of the oracle run
+with the GPU's per-level iteration counts; batched results equal single
+solves bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1602_04386_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+fiedler = pytest.importorskip("paper_1602_04386_gb300.fiedler")
+torch = pytest.importorskip("torch")
+
+FP64, FP32 = 0, 1
+
+
+def setup_module(module):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    fiedler.load()
+
+
+def check_against_oracle(g, precision, lam_tol, tail=4096):
+    with fiedler.Plan(precision=precision, tail_max_n=tail) as p:
+        r = p.solve(g)
+        assert r.status in (fiedler.FIEDLER_OK, fiedler.FIEDLER_ENOTCONVERGED), r
+        counts = [p.level_info(l).pi_iters for l in range(p.num_levels)]
+        ref = oracle.solve(g, forced_pi=counts)
+        assert ref.status == 0 and p.num_levels == ref.num_levels
+        for l in range(p.num_levels):
+            a, b = p.copy_level(l), ref.level(l)
+            assert np.array_equal(a["rowptr"], b.rowptr) and np.array_equal(a["col"], b.col), l
+            assert np.array_equal(a["w"], b.w), l
+            assert np.array_equal(a["color"], b.color), l
+            if l + 1 < p.num_levels:
+                assert np.array_equal(a["agg"], b.agg), l
+    assert abs(r.lambda2 - ref.lam) <= lam_tol * abs(ref.lam), (r.lambda2, ref.lam)
+    return r
+
+
+@pytest.mark.parametrize("scale,seed", [(9, 1), (10, 2), (12, 3)])
+@pytest.mark.parametrize("precision,tol", [(FP64, 1e-10), (FP32, 1e-5)])
+def test_rmat(scale, seed, precision, tol):
+    g = inputs.rmat(scale, seed=seed)
+    check_against_oracle(g, precision, tol)
+
+
+@pytest.mark.parametrize("npts", [2000, 20000])
+@pytest.mark.parametrize("precision,tol", [(FP64, 1e-10), (FP32, 1e-5)])
+def test_knn_mixture(npts, precision, tol):
+    g = inputs.knn_mixture(npts, seed=7)
+    check_against_oracle(g, precision, tol)
+
+
+def test_batch_mix_equals_single_solves():
+    gs = inputs.batch_mix(16, scale_range=(9, 12), side_range=(20, 120))
+    with fiedler.Plan() as p:
+        res = p.solve_batch(gs)
+    for g, r in zip(gs, res):
+        with fiedler.Plan(tail_max_n=1 << 30) as q:
+            a = q.solve(g)
+        assert r.status == a.status == fiedler.FIEDLER_OK
+        assert r.lambda2 == a.lambda2 and np.array_equal(r.x, a.x)

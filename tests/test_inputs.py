@@ -1,0 +1,58 @@
+"""Structure of the seeded synthetic generators (no solver arithmetic)."""
+import numpy as np
+import pytest
+
+from paper_1602_04386_gb300 import inputs
+
+
+def check_csr(g):
+    assert g.rowptr[0] == 0 and g.rowptr[-1] == g.nnz and np.all(np.diff(g.rowptr) >= 0)
+    A = {}
+    for i in range(g.n):
+        cs = g.col[g.rowptr[i]:g.rowptr[i + 1]]
+        assert np.all(np.diff(cs) > 0) and i not in cs
+        for j, w in zip(cs, g.w[g.rowptr[i]:g.rowptr[i + 1]]):
+            A[(i, int(j))] = w
+    for (i, j), w in A.items():
+        assert A[(j, i)] == w and w > 0
+
+
+def connected(g):
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    a = sp.csr_matrix((np.ones(g.nnz), g.col, g.rowptr), shape=(g.n, g.n))
+    return connected_components(a, directed=False)[0] == 1
+
+
+def test_grid_counts_and_weights():
+    g = inputs.grid(7, 5, "uniform", seed=3)
+    assert g.n == 35 and g.nnz == 2 * (7 * 4 + 6 * 5)
+    check_csr(g)
+    assert g.w.dtype == np.float32 and g.w.min() >= 0.5 and g.w.max() < 1.5
+
+
+@pytest.mark.parametrize("scale", [6, 9])
+def test_rmat_structure(scale):
+    g = inputs.rmat(scale, seed=7)
+    check_csr(g)
+    assert connected(g) and g.n <= 2 ** scale
+    assert g.w.min() >= np.float32(0.1) and g.w.max() < 1.0
+    deg = np.diff(g.rowptr)
+    assert deg.max() > 4 * deg.mean()  # skewed degrees
+
+
+def test_knn_structure():
+    g = inputs.knn_mixture(3000, seed=5)
+    check_csr(g)
+    assert connected(g)
+    deg = np.diff(g.rowptr)
+    assert deg.min() >= 1 and np.median(deg) >= 10
+    assert g.w.max() <= 1.0
+
+
+def test_batch_mix_alternates_families():
+    gs = inputs.batch_mix(6, scale_range=(6, 8), side_range=(5, 9))
+    assert [g.name.startswith("grid") for g in gs] == [True, False] * 3
+    for g in gs:
+        check_csr(g)
+        assert connected(g)
