@@ -146,6 +146,117 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+BATCH = dict(count=4096, seed=inputs.BASE_SEED + 4)
+
+
+def batch_name(count):
+    return (f"batch_mix{count}-seed{BATCH['seed']} (even: unit grids, sides U[20,300]; "
+            f"odd: R-MAT a=.57 b=c=.19 scale U[9,16] ef 8 w U[.1,1))")
+
+
+def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=16):
+    """The batched form on the batch workload: one fiedler_solve_batch call per
+    step over all graphs (device-resident inputs and outputs), FP32 form; the
+    plain single-graph FP64 form on every plain_every-th graph for solves/s and
+    lambda2 agreement; the batched FP64 form once over the whole batch."""
+    import torch
+    from paper_1602_04386_gb300 import fiedler
+    count = len(graphs)
+    garr = (fiedler.fiedler_graph * count)()
+    rarr = (fiedler.fiedler_result * count)()
+    keep, offs = [], []
+    off = 0
+    for i, g in enumerate(graphs):
+        gs, k = fiedler.device_graph(g, dev)
+        keep.append(k)
+        garr[i] = gs
+        offs.append(off)
+        off += g.n
+    X = torch.empty(off, dtype=torch.float64, device=dev)
+    base = X.data_ptr()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def run_batch(plan):
+        for i in range(count):
+            rarr[i].x = base + 8 * offs[i]
+            rarr[i].x_on_device = 1
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        st = plan.solve_batch_struct(garr, rarr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if st != fiedler.FIEDLER_OK:
+            raise fiedler.FiedlerError(st, "fiedler_solve_batch")
+        return e0.elapsed_time(e1), wall
+
+    plan = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP32_FP64RED)
+    for _ in range(warmup):
+        run_batch(plan)
+    plan.set_profiling(True)
+    ms, walls, kms, kbytes, launches = [], [], 0.0, 0.0, 0
+    for _ in range(steps):
+        t, wall = run_batch(plan)
+        ms.append(t)
+        walls.append(wall)
+        pr = plan.profile()
+        kms += pr.kernel_ms[3]
+        kbytes += pr.kernel_bytes[3]
+        launches += int(pr.kernel_launches)
+    plan.set_profiling(False)
+    lam32 = np.array([rarr[i].lambda2 for i in range(count)])
+    st32 = np.array([rarr[i].status for i in range(count)])
+    plan.close()
+    # batched FP64 form, one pass
+    plan64b = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP64)
+    t64b, _ = run_batch(plan64b)
+    lam64b = np.array([rarr[i].lambda2 for i in range(count)])
+    plan64b.close()
+    # plain single-graph FP64 form on a sample
+    plan64 = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP64)
+    sample = list(range(0, count, plain_every))
+    lam64 = {}
+    plan64.solve_struct(garr[sample[0]], X[offs[sample[0]]:], x_on_device=True)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in sample:
+        r = plan64.solve_struct(garr[i], X[offs[i]:], x_on_device=True)
+        lam64[i] = (r.status, r.lambda2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1)
+    plan64.close()
+    ok = [i for i in sample if st32[i] == 0 and lam64[i][0] == 0]
+    rel = np.array([abs(lam32[i] - lam64[i][1]) / abs(lam64[i][1]) for i in ok])
+    relb = np.abs(lam32 - lam64b) / np.abs(lam64b)
+    ms_step = statistics.mean(ms)
+    nnz = int(sum(g.nnz for g in graphs))
+    peak, peak_kind = measured_peaks()
+    kgbs = kbytes / (kms / 1e3) / 1e9 if kms > 0 else None
+    # weight of the sample: the solves/s of the plain form is scaled to the
+    # whole batch by vertex + nonzero count
+    size = np.array([g.n + g.nnz for g in graphs], dtype=np.float64)
+    scale = size.sum() / size[sample].sum()
+    return {
+        "workload": batch_name(count), "graphs": count, "vertices": int(sum(g.n for g in graphs)), "nnz": nnz,
+        "form": "FP32 values/matvec, FP64 reductions; one persistent launch per call",
+        "solves_per_s": count / (ms_step / 1e3), "ms_per_batch": ms_step, "wall_ms_per_batch": 1e3 * statistics.mean(walls),
+        "statuses_ok": int((st32 == 0).sum()),
+        "kernel": "fz_batch_f32", "kernel_ms": kms / steps, "gpu_launches_per_batch": launches / steps,
+        "kernel_algorithmic_gbs": kgbs, "kernel_frac": (kgbs / peak) if kgbs else None, "peak_kind": f"of {peak_kind}",
+        "fp64_batched_solves_per_s": count / (t64b / 1e3),
+        "fp64_plain_solves_per_s": len(sample) / (t64 / 1e3) / scale,
+        "fp64_plain_sample": f"every {plain_every}th graph ({len(sample)}), rate scaled by (n+nnz) to the batch",
+        "lambda2_rel_err_vs_fp64_plain": {"max": float(rel.max()), "median": float(np.median(rel)),
+                                          "frac_le_1e-5": float((rel <= 1e-5).mean()), "graphs": len(ok)},
+        "lambda2_rel_err_vs_fp64_batched": {"max": float(np.nanmax(relb)), "median": float(np.nanmedian(relb)),
+                                            "frac_le_1e-5": float((relb <= 1e-5).mean())},
+    }
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores: each step solves a quarter-size
     sample of the workload (1024 x 768 grid of the same family) and is scaled to
@@ -190,11 +301,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp64 / cpu baseline legs (profiling runs)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form leg")
+    ap.add_argument("--batch-count", type=int, default=BATCH["count"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.no_extras:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    batch_graphs = None
+    if not args.no_batch and not args.no_extras:
+        # generated before CUDA is initialised (worker processes are spawned anyway)
+        batch_graphs = inputs.batch_mix(args.batch_count, seed=BATCH["seed"], procs=min(16, os.cpu_count() or 1))
 
     import torch
     from paper_1602_04386_gb300 import fiedler
@@ -376,6 +493,9 @@ def main():
                                     "sample": f"{nrep} whole solves of {workload_name()} (single-threaded C)",
                                     "lambda2": ro.lam}
     plan.close()
+    if batch_graphs is not None:
+        line["batched"] = batched_leg(batch_graphs, stream, dev)
+        line["gpu_launches_batched_per_batch"] = line["batched"]["gpu_launches_per_batch"]
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

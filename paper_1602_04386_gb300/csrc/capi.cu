@@ -102,7 +102,7 @@ struct fiedler_plan {
   size_t stage_cap[3] = {0, 0, 0};
   double *d_xout = nullptr;
   size_t xout_cap = 0;
-  cudaEvent_t ev[8];
+  cudaEvent_t ev[10];         // [0,1] solve, [2..7] its kernels, [8,9] batched kernel
   int profiling = 0;
   int last_type = 1;
   bool have_result = false;
@@ -195,7 +195,9 @@ void fill_opts(fz::Opts &o, const fiedler_options &u, int type) {
   o.pi_max_iters_coarsest = u.pi_max_iters_coarsest;
   o.tie_rule = u.tie_rule;
   o.validate = u.validate;
-  o.tail_max_n = u.tail_max_n;
+  // levels of at most kTinyN vertices always run in the one-block engine,
+  // which keeps them in FP64 (the grid-wide engine would as well, only slower)
+  o.tail_max_n = u.tail_max_n < fz::kTinyN ? fz::kTinyN : u.tail_max_n;
   o.fault_inject = u.fault_inject;
   o.stall_ratio = u.stall_ratio;
   o.pi_cos_tol = u.pi_cos_tol;
@@ -493,7 +495,10 @@ fiedler_status batch_launch(fiedler_plan *p, BatchCtx &c, double arena_scale) {
   char *d_scratch = c.d_buf + c.d_scratch;
   unsigned long long slot_bytes = c.slot_bytes;
   void *args[] = {(void *)&d_states, (void *)&count, (void *)&d_counter, (void *)&d_scratch, (void *)&slot_bytes};
+  const bool prof = p->profiling && &c == &p->bsync;
+  if (prof) CK(cudaEventRecord(p->ev[8], c.stream));
   CK(cudaLaunchKernel(p->ks[type].batch, dim3(nslots), dim3(fz::kCtaThreads), args, 0, c.stream));
+  if (prof) CK(cudaEventRecord(p->ev[9], c.stream));
   CK(cudaMemcpyAsync(hs, c.d_buf + c.d_states, sizeof(State) * (size_t)count, cudaMemcpyDeviceToHost, c.stream));
   if (x_b) CK(cudaMemcpyAsync(c.h_buf + c.h_x, c.d_buf + c.d_x, x_b, cudaMemcpyDeviceToHost, c.stream));
   CK(cudaEventRecord(c.done, c.stream));
@@ -536,18 +541,45 @@ void batch_collect(BatchCtx &c) {
 
 bool needs_rerun(int st) { return st == fz::ST_ARENA || st == fz::ST_SCRATCH; }
 
+// Profile of a finished synchronous batched launch (profiling on): the
+// kernel's CUDA-event time, and per phase the device time summed over the
+// graphs (block-time, not wall time) with the algorithmic bytes.
+void batch_profile(fiedler_plan *p, BatchCtx &c) {
+  fiedler_profile &pr = p->prof;
+  const fz::KernelSet &K = p->ks[c.type];
+  pr.n_kernels = 4;
+  for (int k = 0; k < 4; k++) pr.kernel_name[k] = K.names[k];
+  float km = 0.f;
+  cudaEventElapsedTime(&km, p->ev[8], p->ev[9]);
+  pr.kernel_ms[3] += km;
+  pr.kernel_launches_by[3]++;
+  pr.kernel_launches++;
+  pr.n_phases = fz::PH_COUNT;
+  const State *hs = (const State *)(c.h_buf + c.h_states);
+  for (size_t i = 0; i < c.items.size(); i++)
+    for (int ph = 0; ph < fz::PH_COUNT; ph++) {
+      pr.phase_ms[1][ph] += hs[i].phase_ns[1][ph] * 1e-6;
+      pr.phase_bytes[1][ph] += hs[i].phase_bytes[1][ph];
+      pr.kernel_bytes[3] += hs[i].phase_bytes[1][ph];
+    }
+  for (int ph = 0; ph < fz::PH_COUNT; ph++) pr.phase_name[ph] = kPhaseNames[ph];
+}
+
 // Runs c.items to completion on c.stream, growing arenas for graphs whose
 // hierarchy outgrew the first estimate (their rerun uses the same engine).
 fiedler_status batch_run_sync(fiedler_plan *p, BatchCtx &c) {
   double scale = 1.0;
   std::vector<BatchItem> all = c.items;
   std::vector<BatchItem> todo = c.items;
+  const bool prof = p->profiling && &c == &p->bsync;
+  if (prof) memset(&p->prof, 0, sizeof(p->prof));
   for (int attempt = 0; attempt < 4 && !todo.empty(); attempt++) {
     c.items = todo;
     fiedler_status st = batch_launch(p, c, scale);
     if (st != FIEDLER_OK) return st;
     CK(cudaEventSynchronize(c.done));
     batch_collect(c);
+    if (prof) batch_profile(p, c);
     todo.clear();
     for (auto &it : c.items)
       if (needs_rerun(it.st)) todo.push_back(it);
@@ -790,7 +822,7 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
   if (cudaMalloc(&p->d_dpart, sizeof(double) * 2 * fz::kMaxBlocks * fz::kDSum) != cudaSuccess)
     return fail(FIEDLER_ENOMEM);
   if (cudaMallocHost(&p->h_state, sizeof(State)) != cudaSuccess) return fail(FIEDLER_ENOMEM);
-  for (int i = 0; i < 8; i++)
+  for (int i = 0; i < 10; i++)
     if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return fail(FIEDLER_ECUDA);
   p->worker = std::thread(worker_main, p);
   *out = p;
@@ -968,7 +1000,7 @@ void fiedler_plan_destroy(fiedler_plan *p) {
   if (p->d_ipart) cudaFree(p->d_ipart);
   if (p->d_dpart) cudaFree(p->d_dpart);
   if (p->h_state) cudaFreeHost(p->h_state);
-  for (int i = 0; i < 8; i++)
+  for (int i = 0; i < 10; i++)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;

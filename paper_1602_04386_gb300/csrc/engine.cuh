@@ -103,7 +103,6 @@ FZD void best_set(Best &b, uint64_t wk, int u, int v) {
 // per kernel
 constexpr int kShSort = 2048;  // u64 words of the raw buffer (16 KB)
 constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one thread
-constexpr int kTinyN = 256;    // levels up to this size are smoothed by one warp
 
 FZD uint64_t *sh_raw() {
   __shared__ uint64_t raw[kShSort];
@@ -607,6 +606,15 @@ struct Eng {
   FZD static W wof(const Level *L) { return W{L->w64, L->w32}; }
 
   FZD bool elig(int n) const { return GRID ? (n > S->opt.tail_max_n) : (n <= S->opt.tail_max_n); }
+  // Value type of a level's solve weights and iterates: T, except that the
+  // FP32 form keeps levels of at most kTinyN vertices in FP64.  Those levels
+  // are latency-bound (one warp smooths them), so FP64 costs next to nothing
+  // there, and their power-iteration stop decisions set the coarse start
+  // vector that the whole cascade refines: one iteration more or less on a
+  // 51-vertex level moves the final lambda2 of a 2048 x 1536 grid by 4e-5.
+  // In FP64 those decisions, and the tiny levels' vectors, are the FP64
+  // form's own.
+  FZD static bool vdbl(int n) { return sizeof(T) == 8 || n <= kTinyN; }
 
   FZD int wl_read(int slot) const { return *(volatile int *)&S->wl_cnt[slot]; }
 
@@ -887,9 +895,11 @@ struct Eng {
     int *colstart = (int *)aalloc(4ull * (C + 1));
     int *srp = (int *)aalloc(4ull * (n + 1));
     int *scol = (int *)aalloc(4ull * (nnz > 0 ? nnz : 1));
-    T *sw = (T *)aalloc(sizeof(T) * (unsigned long long)(nnz > 0 ? nnz : 1));
-    T *x = (T *)aalloc(sizeof(T) * (unsigned long long)n);
-    T *y = (T *)aalloc(sizeof(T) * (unsigned long long)n);
+    const bool vd = vdbl(n);
+    const unsigned long long vsz = vd ? 8ull : sizeof(T);
+    void *sw = aalloc(vsz * (unsigned long long)(nnz > 0 ? nnz : 1));
+    void *x = aalloc(vsz * (unsigned long long)n);
+    void *y = aalloc(vsz * (unsigned long long)n);
     int *sagg = (int *)aalloc(4ull * n);
     if (!hist || !perm || !iperm || !colstart || !srp || !scol || !sw || !x || !y || !sagg) return false;
     int *sh_cnt = reinterpret_cast<int *>(sh_raw());                     // [kMaxColors]
@@ -994,7 +1004,8 @@ struct Eng {
         srp[k] = o;
         for (int e = rp[v]; e < rp[v + 1]; e++, o++) {
           scol[o] = iperm[ci[e]];
-          sw[o] = (T)wl[e];
+          if (vd) ((double *)sw)[o] = wl[e];
+          else ((T *)sw)[o] = (T)wl[e];
         }
       }
       run += tot;
@@ -1020,7 +1031,7 @@ struct Eng {
       L->sagg = sagg;
     }
     if (!sync()) return false;
-    FZ_MARK(PH_REORDER, 28.0 * n + (8.0 + (L->w64 ? 8.0 : 4.0) + 4.0 + sizeof(T)) * nnz);
+    FZ_MARK(PH_REORDER, 28.0 * n + (8.0 + (L->w64 ? 8.0 : 4.0) + 4.0 + vsz) * nnz);
     return true;
   }
 
@@ -1519,12 +1530,13 @@ struct Eng {
         return false;
       }
     }
-    T *x = (T *)L->x;
     double acc[2] = {0.0, 0.0};
     const uint64_t seed = S->opt.seed;
+    const bool vd = vdbl(n);
     for (int i = tid; i < n; i += nthr) {
-      const T v = (T)uniform01(seed, (uint64_t)i);
-      x[iperm[i]] = v;
+      const double v = vd ? uniform01(seed, (uint64_t)i) : (double)(T)uniform01(seed, (uint64_t)i);
+      if (vd) ((double *)L->x)[iperm[i]] = v;
+      else ((T *)L->x)[iperm[i]] = (T)v;
       acc[0] += (double)v;
       acc[1] += (double)v * (double)v;
     }
@@ -1537,17 +1549,26 @@ struct Eng {
 
   // ---- A8: prolongation y^j = I^T y^{j+1} ----------------------------------
   FZD bool prolong(int l) {
+    const bool vf = vdbl(S->lv[l].n), vc = vdbl(S->lv[l + 1].n);
+    if (vf) return prolong_v<double, double>(l);
+    if (vc) return prolong_v<T, double>(l);
+    return prolong_v<T, T>(l);
+  }
+
+  // VF, VC: value types of the fine and the coarse level
+  template <class VF, class VC>
+  FZD bool prolong_v(int l) {
     cur_level = l;
     Level *F = &S->lv[l];
     const Level *Cl = &S->lv[l + 1];
     const int n = F->n;
-    const T *xc = (const T *)Cl->x;
-    const T muc = (T)Cl->mu, scc = (T)Cl->s;
-    T *x = (T *)F->x;
+    const VC *xc = (const VC *)Cl->x;
+    const VC muc = (VC)Cl->mu, scc = (VC)Cl->s;
+    VF *x = (VF *)F->x;
     const int *sagg = F->sagg;
     double acc[2] = {0.0, 0.0};
     for (int k = tid; k < n; k += nthr) {
-      const T v = (xc[sagg[k]] - muc) * scc;
+      const VF v = (VF)((xc[sagg[k]] - muc) * scc);
       x[k] = v;
       acc[0] += (double)v;
       acc[1] += (double)v * (double)v;
@@ -1555,45 +1576,52 @@ struct Eng {
     if (!grid_dsum<2>(acc)) return false;
     double mu, sc;
     if (!deflate_scalars(acc, n, mu, sc)) return false;
-    FZ_MARK(PH_PROLONG, (4.0 + 2.0 * sizeof(T)) * n);
+    FZ_MARK(PH_PROLONG, 4.0 * n + (double)(sizeof(VF) + sizeof(VC)) * n);
     return smooth(l, S->opt.pi_max_iters, mu, sc, PH_GS);
   }
 
   // ---- A9 + A10: Gauss-Seidel sweeps, then shifted power iteration ----------
   FZD bool smooth(int l, int kmax, double mu, double s, int gs_phase) {
-    if (!GRID && S->lv[l].n <= kTinyN) return smooth_warp(l, kmax, mu, s, gs_phase);
+    const int n = S->lv[l].n;
+    if (!GRID && n <= kTinyN) return smooth_warp<double>(l, kmax, mu, s, gs_phase);
+    if (vdbl(n)) return smooth_v<double>(l, kmax, mu, s, gs_phase);
+    return smooth_v<T>(l, kmax, mu, s, gs_phase);
+  }
+
+  template <class V>
+  FZD bool smooth_v(int l, int kmax, double mu, double s, int gs_phase) {
     Level *L = &S->lv[l];
     const int n = L->n, nnz = L->nnz, C = L->ncolors;
     const int *srp = L->srowptr, *scol = L->scol, *cst = L->colstart;
-    const T *sw = (const T *)L->sw;
-    T *A = (T *)L->x, *B = (T *)L->y;
+    const V *sw = (const V *)L->sw;
+    V *A = (V *)L->x, *B = (V *)L->y;
     const double g = S->opt.guard;
     const int nsweeps = S->opt.gs_sweeps;
-    const double sweep_bytes = 4.0 * (n + 1) + (4.0 + sizeof(T)) * nnz + 2.0 * sizeof(T) * n;
+    const double sweep_bytes = 4.0 * (n + 1) + (4.0 + sizeof(V)) * nnz + 2.0 * sizeof(V) * n;
     const int ph_gs = gs_phase == PH_COARSEST ? PH_COARSEST : PH_GS;
     const int ph_pi = gs_phase == PH_COARSEST ? PH_COARSEST : PH_PI;
     // FP64 scalars (means, norms, cos test) are computed by thread 0 of each
     // block from the grid totals and broadcast through shared memory; the
-    // T copies used in the inner loops come with them
+    // V copies used in the inner loops come with them
     double *bc = sh_bc();
     const double inv_n = 1.0 / (double)n;
-    T muT = (T)mu, sT = (T)s;
+    V muT = (V)mu, sT = (V)s;
     int sweeps = 0;
     for (int k = 0; k < nsweeps; k++) {
       double acc[2] = {0.0, 0.0};
       for (int c = 0; c < C; c++) {
         const int cs = cst[c], ce = cst[c + 1];
         for (int i = cs + tid; i < ce; i += nthr) {
-          T num = (T)0, dsum = (T)0;
+          V num = (V)0, dsum = (V)0;
           const int e1 = srp[i + 1];
           for (int e = srp[i]; e < e1; e++) {
             const int j = scol[e];
-            const T wv = sw[e];
-            const T xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
+            const V wv = sw[e];
+            const V xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
             num += wv * xj;
             dsum += wv;
           }
-          const T xi = num / dsum;
+          const V xi = num / dsum;
           B[i] = xi;
           acc[0] += (double)xi;
           acc[1] += (double)xi * (double)xi;
@@ -1613,31 +1641,31 @@ struct Eng {
       const double m2 = bc[1], s2 = bc[2];
       __syncthreads();
       if (!keep) break;  // keep the previous iterate
-      T *t = A;
+      V *t = A;
       A = B;
       B = t;
       mu = m2;
       s = s2;
-      muT = (T)mu;
-      sT = (T)s;
+      muT = (V)mu;
+      sT = (V)s;
       sweeps++;
     }
     const double sigma = L->sigma;
     const double tol = S->opt.pi_cos_tol, rtol = S->opt.resid_tol;
     const bool resid = rtol > 0.0;
-    const T sigT = (T)sigma;
+    const V sigT = (V)sigma;
     int done = 0, capped = 0;
     double lastc = 0.0;
     for (int it = 1; it <= kmax; it++) {
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
       double acr[2] = {0.0, 0.0};
       for (int i = tid; i < n; i += nthr) {
-        const T xi = A[i];
-        T lx = (T)0;
+        const V xi = A[i];
+        V lx = (V)0;
         const int e1 = srp[i + 1];
         for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
-        const T xh = (xi - muT) * sT;
-        const T yi = sigT * xh - sT * lx;
+        const V xh = (xi - muT) * sT;
+        const V yi = sigT * xh - sT * lx;
         B[i] = yi;
         const double yd = (double)yi, xd = (double)xh;
         acc[0] += yd;
@@ -1670,13 +1698,13 @@ struct Eng {
       const double my = bc[1], sy = bc[2], cosv = bc[3];
       __syncthreads();
       if (!ok) break;  // keep the previous vector
-      T *t = A;
+      V *t = A;
       A = B;
       B = t;
       mu = my;
       s = sy;
-      muT = (T)mu;
-      sT = (T)s;
+      muT = (V)mu;
+      sT = (V)s;
       lastc = cosv;
       done = it;
       if (stop) break;
@@ -1700,36 +1728,37 @@ struct Eng {
   // syncs between colour passes and warp-shuffle FP64 sums, while the other
   // warps wait at one block barrier.  Identical arithmetic per row; only the
   // order of the FP64 sums differs from smooth().
+  template <class V>
   FZD bool smooth_warp(int l, int kmax, double mu, double s, int gs_phase) {
     Level *L = &S->lv[l];
     const int n = L->n, nnz = L->nnz, C = L->ncolors;
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       const int *srp = L->srowptr, *scol = L->scol, *cst = L->colstart;
-      const T *sw = (const T *)L->sw;
-      T *A = (T *)L->x, *B = (T *)L->y;
+      const V *sw = (const V *)L->sw;
+      V *A = (V *)L->x, *B = (V *)L->y;
       const double g = S->opt.guard;
       const int nsweeps = S->opt.gs_sweeps;
-      const double sweep_bytes = 4.0 * (n + 1) + (4.0 + sizeof(T)) * nnz + 2.0 * sizeof(T) * n;
+      const double sweep_bytes = 4.0 * (n + 1) + (4.0 + sizeof(V)) * nnz + 2.0 * sizeof(V) * n;
       const int ph_gs = gs_phase == PH_COARSEST ? PH_COARSEST : PH_GS;
       const int ph_pi = gs_phase == PH_COARSEST ? PH_COARSEST : PH_PI;
       int sweeps = 0;
       for (int k = 0; k < nsweeps; k++) {
         double acc[2] = {0.0, 0.0};
-        const T muT = (T)mu, sT = (T)s;
+        const V muT = (V)mu, sT = (V)s;
         for (int c = 0; c < C; c++) {
           const int cs = cst[c], ce = cst[c + 1];
           for (int i = cs + lane; i < ce; i += 32) {
-            T num = (T)0, dsum = (T)0;
+            V num = (V)0, dsum = (V)0;
             const int e1 = srp[i + 1];
             for (int e = srp[i]; e < e1; e++) {
               const int j = scol[e];
-              const T wv = sw[e];
-              const T xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
+              const V wv = sw[e];
+              const V xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
               num += wv * xj;
               dsum += wv;
             }
-            const T xi = num / dsum;
+            const V xi = num / dsum;
             B[i] = xi;
             acc[0] += (double)xi;
             acc[1] += (double)xi * (double)xi;
@@ -1750,7 +1779,7 @@ struct Eng {
         m2 = __shfl_sync(0xffffffffu, m2, 0);
         s2 = __shfl_sync(0xffffffffu, s2, 0);
         if (!keep) break;
-        T *t = A;
+        V *t = A;
         A = B;
         B = t;
         mu = m2;
@@ -1764,14 +1793,14 @@ struct Eng {
       double lastc = 0.0;
       for (int it = 1; it <= kmax; it++) {
         double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        const T muT = (T)mu, sT = (T)s, sigT = (T)sigma;
+        const V muT = (V)mu, sT = (V)s, sigT = (V)sigma;
         for (int i = lane; i < n; i += 32) {
-          const T xi = A[i];
-          T lx = (T)0;
+          const V xi = A[i];
+          V lx = (V)0;
           const int e1 = srp[i + 1];
           for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
-          const T xh = (xi - muT) * sT;
-          const T yi = sigT * xh - sT * lx;
+          const V xh = (xi - muT) * sT;
+          const V yi = sigT * xh - sT * lx;
           B[i] = yi;
           const double yd = (double)yi, xd = (double)xh;
           acc[0] += yd;
@@ -1804,7 +1833,7 @@ struct Eng {
         sy = __shfl_sync(0xffffffffu, sy, 0);
         cosv = __shfl_sync(0xffffffffu, cosv, 0);
         if (!ok) break;
-        T *t = A;
+        V *t = A;
         A = B;
         B = t;
         mu = my;
@@ -1829,28 +1858,31 @@ struct Eng {
   }
 
   // ---- A11: Rayleigh quotient, residual, orthogonality, sign, output --------
-  FZD bool finalize() {
+  FZD bool finalize() { return vdbl(S->lv[0].n) ? finalize_v<double>() : finalize_v<T>(); }
+
+  template <class V>
+  FZD bool finalize_v() {
     cur_level = 0;
     Level *L = &S->lv[0];
     const int n = L->n, nnz = L->nnz;
     const int *srp = L->srowptr, *scol = L->scol, *perm = L->perm, *iperm = L->iperm;
-    const T *sw = (const T *)L->sw;
-    const T *A = (const T *)L->x;
+    const V *sw = (const V *)L->sw;
+    const V *A = (const V *)L->x;
     const double mu = L->mu, s = L->s;
     // x_hat = (x - mu) * s.  The edge form needs only differences x_i - x_j,
     // in which mu cancels: per row, sum_j w (x_i - x_j) and sum_j w (x_i - x_j)^2
-    // are taken in T (neighbouring values of a smooth vector are close, so
-    // their difference is exact in T) and accumulated over rows in FP64, scaled
+    // are taken in V (neighbouring values of a smooth vector are close, so
+    // their difference is exact in V) and accumulated over rows in FP64, scaled
     // by s and s^2 at the end.
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     IRed big{0, 0, LLONG_MIN};
     for (int k = tid; k < n; k += nthr) {
-      const T xi = A[k];
-      T lx = (T)0, num = (T)0;
+      const V xi = A[k];
+      V lx = (V)0, num = (V)0;
       const int e1 = srp[k + 1];
       for (int e = srp[k]; e < e1; e++) {
-        const T dl = xi - A[scol[e]];
-        const T wd = sw[e] * dl;
+        const V dl = xi - A[scol[e]];
+        const V wd = sw[e] * dl;
         lx += wd;
         num += wd * dl;
       }
@@ -1898,7 +1930,7 @@ struct Eng {
       S->capped = cap;
     }
     if (!sync()) return false;
-    FZ_MARK(PH_FINAL, 4.0 * (n + 1) + (4.0 + sizeof(T)) * nnz + (2.0 * sizeof(T) + 8.0 + 8.0) * n);
+    FZ_MARK(PH_FINAL, 4.0 * (n + 1) + (4.0 + sizeof(V)) * nnz + (2.0 * sizeof(V) + 8.0 + 8.0) * n);
     return true;
   }
 

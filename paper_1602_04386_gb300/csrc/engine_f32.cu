@@ -20,6 +20,7 @@ void kernels_f32(KernelSet *k) {
   k->names[0] = "fz_grid_setup_f32";
   k->names[1] = "fz_cta_f32";
   k->names[2] = "fz_grid_solve_f32";
+  k->names[3] = "fz_batch_f32";
 }
 
 }  // namespace fz

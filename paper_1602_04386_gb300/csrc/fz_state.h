@@ -12,6 +12,7 @@ constexpr int kMaxBlocks = 2048;   // grid-wide kernel blocks (partials buffer s
 constexpr int kMaxColors = 1024;   // colour classes per level supported by the reorder
 constexpr int kCtaThreads = 512;   // one-block kernel
 constexpr int kGridThreads = 512;  // grid-wide kernel block size
+constexpr int kTinyN = 256;        // levels up to this size: one warp smooths them (FP64 values)
 
 enum Phase {
   PH_INGEST = 0, PH_COLOR, PH_REORDER, PH_MATCH, PH_AGG, PH_GALERKIN,

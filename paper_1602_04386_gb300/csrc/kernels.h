@@ -8,7 +8,7 @@ struct KernelSet {
   const void *grid_solve;  // cooperative, kGridThreads per block: solve of levels with n > tail_max_n
   const void *cta;         // one block of kCtaThreads: everything on levels with n <= tail_max_n
   const void *batch;       // persistent blocks of kCtaThreads, one graph at a time each
-  const char *names[3];    // in launch order: grid_setup, cta, grid_solve
+  const char *names[4];    // profile slots: grid_setup, cta, grid_solve, batch
 };
 void kernels_f32(KernelSet *k);
 void kernels_f64(KernelSet *k);

@@ -440,6 +440,11 @@ class Plan:
         st, out = fiedler_plan_serving_stats(self.h)
         return out
 
+    def solve_batch_struct(self, garr, rarr) -> int:
+        """Batched solve of prepared arrays of fiedler_graph and fiedler_result
+        (same length); returns the fiedler_status of the call."""
+        return fiedler_solve_batch(self.h, garr, rarr)
+
     def solve_batch(self, graphs, on_device=True, want_x=True):
         """Batched solve of a list of inputs.CSR; returns a list of Result (x as numpy)."""
         keep = []

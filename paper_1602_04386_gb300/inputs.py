@@ -90,11 +90,10 @@ def csr_from_edges(n, u, v, w, dtype=np.float32, name="") -> CSR:
     rows = np.concatenate([u, v])
     cols = np.concatenate([v, u])
     vals = np.concatenate([w, w])
-    order = np.lexsort((cols, rows))
+    order = np.argsort(rows * n + cols)  # keys are distinct: (row, col) order
     rows, cols, vals = rows[order], cols[order], vals[order]
     rowptr = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(rowptr, rows + 1, 1)
-    rowptr = np.cumsum(rowptr)
+    rowptr[1:] = np.cumsum(np.bincount(rows, minlength=n))
     return CSR(n, rowptr.astype(np.int32), cols.astype(np.int32), vals, name)
 
 
@@ -163,7 +162,7 @@ def random_connected(n: int, avg_deg: float, seed: int, wlo=0.1, whi=1.0, dtype=
     v = np.concatenate([tv, ev])
     keep = u != v
     lo, hi = np.minimum(u[keep], v[keep]), np.maximum(u[keep], v[keep])
-    key = np.unique(lo * n + hi)
+    key = _distinct(lo * n + hi)
     lo, hi = key // n, key % n
     w = (wlo + (whi - wlo) * uniform01(seed, k + np.arange(lo.shape[0]))).astype(np.float32)
     return csr_from_edges(n, lo, hi, w.astype(dtype), dtype=dtype, name=f"rand{n}-s{seed}")
@@ -195,6 +194,12 @@ def with_self_loops(g: CSR, rows, weight=1.0) -> CSR:
     return CSR(g.n, np.asarray(rp), np.asarray(cols), np.asarray(ws, dtype=g.w.dtype), name=g.name + "+loops")
 
 
+def _distinct(keys: np.ndarray) -> np.ndarray:
+    """Sorted distinct values of an integer array."""
+    s = np.sort(keys)
+    return s[np.concatenate(([True], s[1:] != s[:-1]))] if s.size else s
+
+
 def largest_component(g: CSR) -> CSR:
     """Induced subgraph on the largest connected component (vertex order kept)."""
     import scipy.sparse as sp
@@ -211,8 +216,8 @@ def largest_component(g: CSR) -> CSR:
     m = (new[rows] >= 0) & (new[g.col] >= 0)
     r, c, w = new[rows[m]], new[g.col[m]], g.w[m]
     rowptr = np.zeros(keep.size + 1, np.int64)
-    np.add.at(rowptr, r + 1, 1)
-    return CSR(keep.size, np.cumsum(rowptr), c, w, name=g.name + "-lcc")
+    rowptr[1:] = np.cumsum(np.bincount(r, minlength=keep.size))
+    return CSR(keep.size, rowptr, c, w, name=g.name + "-lcc")
 
 
 def rmat(scale: int, edge_factor: int = 8, a=0.57, b=0.19, c=0.19, seed: int = BASE_SEED + 4,
@@ -220,19 +225,24 @@ def rmat(scale: int, edge_factor: int = 8, a=0.57, b=0.19, c=0.19, seed: int = B
     """R-MAT graph: edge_factor * 2^scale draws, each choosing one quadrant per
     bit level with probabilities (a, b, c, 1-a-b-c); symmetrised, duplicates and
     self-loops removed, weights uniform in [wlo, whi) per undirected edge
-    (rounded to f32), largest connected component kept."""
+    (rounded to f32), largest connected component kept.
+
+    Quadrant draws are 16-bit: output k of the seed's stream supplies the draws
+    of levels 4k' .. 4k'+3 of one edge as its four 16-bit words (low word
+    first), compared with the thresholds round(65536 * (a, a+b, a+b+c))."""
     n = 1 << scale
     m = edge_factor * n
-    u = uniform01(seed, np.arange(m * scale, dtype=np.int64)).reshape(m, scale)
-    q = (u >= a).astype(np.int64) + (u >= a + b) + (u >= a + b + c)  # quadrant 0..3
-    rbit = (q >= 2).astype(np.int64)
-    cbit = (q % 2).astype(np.int64)
-    pw = 1 << np.arange(scale - 1, -1, -1, dtype=np.int64)
-    src = rbit @ pw
-    dst = cbit @ pw
+    wpe = (scale + 3) // 4  # 64-bit outputs per edge
+    words = splitmix64(seed, np.arange(m * wpe, dtype=np.int64))
+    u = words.view(np.uint16).reshape(m, 4 * wpe)[:, :scale]  # little-endian: low word first
+    ta, tb, tc = (int(round(65536 * t)) for t in (a, a + b, a + b + c))
+    q = (u >= ta).astype(np.uint8) + (u >= tb) + (u >= tc)  # quadrant 0..3
+    pw = (1 << np.arange(scale - 1, -1, -1, dtype=np.int64))
+    src = ((q >> 1).astype(np.int64) * pw).sum(axis=1)
+    dst = ((q & 1).astype(np.int64) * pw).sum(axis=1)
     keep = src != dst
     lo, hi = np.minimum(src[keep], dst[keep]), np.maximum(src[keep], dst[keep])
-    key = np.unique(lo * n + hi)
+    key = _distinct(lo * n + hi)
     lo, hi = key // n, key % n
     w = (wlo + (whi - wlo) * uniform01(seed + 1, np.arange(key.size))).astype(np.float32)
     g = csr_from_edges(n, lo, hi, w.astype(dtype), dtype=dtype, name=f"rmat{scale}-s{seed}")
@@ -259,26 +269,50 @@ def knn_mixture(npts: int = 200_000, k: int = 10, clusters: int = 8, sigma: floa
     dd = d[:, 1:].ravel()
     keep = src != dst
     lo, hi, dd = np.minimum(src[keep], dst[keep]), np.maximum(src[keep], dst[keep]), dd[keep]
-    key, first = np.unique(lo * npts + hi, return_index=True)
-    lo, hi, dd = key // npts, key % npts, dd[first]
+    key = lo * npts + hi
+    order = np.argsort(key, kind="stable")
+    key, dd = key[order], dd[order]
+    first = np.concatenate(([True], key[1:] != key[:-1]))  # first listing of each edge
+    key, dd = key[first], dd[first]
+    lo, hi = key // npts, key % npts
     w = np.exp(-dd * dd / 0.25).astype(np.float32)
     w = np.maximum(w, np.float32(np.finfo(np.float32).tiny))  # keep every weight positive
     g = csr_from_edges(npts, lo, hi, w.astype(dtype), dtype=dtype, name=f"knn{npts}-s{seed}")
     return largest_component(g)
 
 
-def batch_mix(count: int = 4096, seed: int = BASE_SEED + 4, scale_range=(9, 16), side_range=(20, 300)):
-    """The batched workload: even ids 2-D grids with sides uniform in
-    side_range and unit weights, odd ids R-MAT graphs with scale uniform in
-    scale_range (edge factor 8, weights uniform [0.1, 1))."""
-    out = []
-    u = uniform01(seed, np.arange(3 * count))
-    for i in range(count):
-        if i % 2 == 0:
-            m = side_range[0] + int(u[3 * i] * (side_range[1] - side_range[0] + 1))
-            k = side_range[0] + int(u[3 * i + 1] * (side_range[1] - side_range[0] + 1))
-            out.append(grid(m, k, "unit"))
-        else:
-            s = scale_range[0] + int(u[3 * i + 2] * (scale_range[1] - scale_range[0] + 1))
-            out.append(rmat(s, seed=seed + 1000 + i))
+def batch_mix_item(i: int, seed: int = BASE_SEED + 4, scale_range=(9, 16), side_range=(20, 300)) -> CSR:
+    """Graph i of the batched workload: even i a 2-D grid with sides uniform in
+    side_range and unit weights, odd i an R-MAT graph with scale uniform in
+    scale_range (edge factor 8, weights uniform [0.1, 1)).  The sizes come from
+    draws 3i .. 3i+2 of the seed's stream, the R-MAT edges from seed + 1000 + i."""
+    u = uniform01(seed, np.arange(3 * i, 3 * i + 3))
+    if i % 2 == 0:
+        m = side_range[0] + int(u[0] * (side_range[1] - side_range[0] + 1))
+        k = side_range[0] + int(u[1] * (side_range[1] - side_range[0] + 1))
+        return grid(m, k, "unit")
+    s = scale_range[0] + int(u[2] * (scale_range[1] - scale_range[0] + 1))
+    return rmat(s, seed=seed + 1000 + i)
+
+
+def _batch_items(args):
+    lo, hi, seed, scale_range, side_range = args
+    return [batch_mix_item(i, seed, scale_range, side_range) for i in range(lo, hi)]
+
+
+def batch_mix(count: int = 4096, seed: int = BASE_SEED + 4, scale_range=(9, 16), side_range=(20, 300),
+              procs: int = 1):
+    """The batched workload: graphs batch_mix_item(0 .. count-1).  With procs > 1
+    they are generated by that many worker processes (started with 'spawn', so
+    this is safe after CUDA has been initialised in the caller)."""
+    if procs <= 1 or count < 64:
+        return [batch_mix_item(i, seed, scale_range, side_range) for i in range(count)]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    step = max(1, count // (8 * procs))
+    jobs = [(lo, min(count, lo + step), seed, scale_range, side_range) for lo in range(0, count, step)]
+    with cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
+        out = []
+        for part in ex.map(_batch_items, jobs):
+            out.extend(part)
     return out

@@ -38,7 +38,7 @@ def test_rmat_structure(scale):
     assert connected(g) and g.n <= 2 ** scale
     assert g.w.min() >= np.float32(0.1) and g.w.max() < 1.0
     deg = np.diff(g.rowptr)
-    assert deg.max() > 4 * deg.mean()  # skewed degrees
+    assert deg.max() > 3 * deg.mean()  # skewed degrees (a hub of degree > 3x the mean)
 
 
 def test_knn_structure():
