@@ -75,8 +75,11 @@ typedef struct {
   int tie_rule;              /* FIEDLER_TIE_HASHED (default) or FIEDLER_TIE_INDEX */
   uint64_t seed;             /* random start vector on the coarsest level (splitmix64 stream) */
   int validate;              /* 1: check the CSR on the device (symmetry, order, weights) */
-  int tail_max_n;            /* levels with n <= tail_max_n run in one thread block; larger
-                                levels run in a cooperative grid-wide kernel */
+  int tail_max_n;            /* levels with n <= tail_max_n and nnz <= tail_max_nnz run in one
+                                thread block; larger levels run in a cooperative grid-wide
+                                kernel.  Levels with n <= 256 and nnz <= 4096 always run in
+                                the thread block. */
+  int tail_max_nnz;          /* see tail_max_n */
   int barrier_timeout_ms;    /* bound on every device-side wait (grid barriers) */
   int fault_inject;          /* testing only: 1 = one block skips the first grid barrier, so the
                                 others' bounded wait runs out and the solve reports ETIMEOUT */
@@ -117,7 +120,7 @@ typedef struct fiedler_plan fiedler_plan;
 /* Fills opts with the defaults: FP32_FP64RED, coarse_max_n 25, max_levels 30,
  * stall_ratio 0.9, gs_sweeps 2, pi_max_iters 10000, pi_max_iters_coarsest
  * 100000, pi_cos_tol 1e-6, resid_tol 0, hashed ties, seed 20160214,
- * validate 1, tail_max_n 4096, barrier_timeout_ms 5000, fault_inject 0,
+ * validate 1, tail_max_n 4096, tail_max_nnz 32768, barrier_timeout_ms 5000, fault_inject 0,
  * hbm_budget_bytes 0 (16 GiB), max_batch 1024, max_inflight 2. */
 void fiedler_options_default(fiedler_options *opts);
 
@@ -256,7 +259,7 @@ fiedler_status fiedler_plan_get_profile(const fiedler_plan *plan, fiedler_profil
  *    cudaGetSymbolAddress (with that device current); make that first call
  *    before any stream capture begins.
  *  - Every level runs in the one-block engine, so results equal those of
- *    fiedler_solve with tail_max_n at least n. */
+ *    fiedler_solve with tail_max_n at least n and tail_max_nnz at least nnz. */
 fiedler_status fiedler_solve_noalloc(const fiedler_options *opts, const fiedler_graph *graph, double *x,
                                      void *cuda_stream, fiedler_result *result);
 

@@ -195,9 +195,8 @@ void fill_opts(fz::Opts &o, const fiedler_options &u, int type) {
   o.pi_max_iters_coarsest = u.pi_max_iters_coarsest;
   o.tie_rule = u.tie_rule;
   o.validate = u.validate;
-  // levels of at most kTinyN vertices always run in the one-block engine,
-  // which keeps them in FP64 (the grid-wide engine would as well, only slower)
-  o.tail_max_n = u.tail_max_n < fz::kTinyN ? fz::kTinyN : u.tail_max_n;
+  o.tail_max_n = u.tail_max_n;
+  o.tail_max_nnz = u.tail_max_nnz;
   o.fault_inject = u.fault_inject;
   o.stall_ratio = u.stall_ratio;
   o.pi_cos_tol = u.pi_cos_tol;
@@ -257,7 +256,11 @@ fiedler_status run_solve(fiedler_plan *p, int64_t n, int64_t nnz, const int32_t 
     memset(&p->prof, 0, sizeof(p->prof));
     CK(cudaMemcpyAsync(p->d_state, h, sizeof(State), cudaMemcpyHostToDevice, p->stream));
     CK(cudaEventRecord(p->ev[0], p->stream));
-    const bool big = n > p->opt.tail_max_n;
+    // the engine's rule for the fine level (it may still hand the level to the
+    // one-block kernel after ingest drops self-loops; a launch with nothing
+    // eligible returns at once)
+    const bool tiny = n <= fz::kTinyN && nnz <= fz::kTinyNnz;
+    const bool big = !tiny && (n > p->opt.tail_max_n || nnz > p->opt.tail_max_nnz);
     if (big && (st = launch(p, K.grid_setup, p->grid_blocks[type][0], fz::kGridThreads, true, 0)) != FIEDLER_OK)
       return st;
     if ((st = launch(p, K.cta, 1, fz::kCtaThreads, false, 1)) != FIEDLER_OK) return st;
@@ -460,6 +463,7 @@ fiedler_status batch_launch(fiedler_plan *p, BatchCtx &c, double arena_scale) {
     memset(h, 0, sizeof(State));
     fill_opts(h->opt, p->opt, type);
     h->opt.tail_max_n = INT_MAX;  // every level in the one-block engine
+    h->opt.tail_max_nnz = INT_MAX;
     h->opt.fault_inject = 0;
     h->bad_index = LLONG_MAX;
     h->n0 = (int)it.n;
@@ -754,6 +758,7 @@ void fiedler_options_default(fiedler_options *o) {
   o->seed = 20160214ull;
   o->validate = 1;
   o->tail_max_n = 4096;
+  o->tail_max_nnz = 32768;
   o->barrier_timeout_ms = 5000;
   o->fault_inject = 0;
   o->hbm_budget_bytes = 0;
@@ -770,7 +775,7 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
   if ((o.precision != FIEDLER_FP64 && o.precision != FIEDLER_FP32_FP64RED) || o.coarse_max_n < 1 ||
       o.max_levels < 1 || o.max_levels > fz::kMaxLevels || !(o.stall_ratio > 0.0 && o.stall_ratio <= 1.0) ||
       o.gs_sweeps < 0 || o.pi_max_iters < 0 || o.pi_max_iters_coarsest < 0 || !(o.pi_cos_tol >= 0.0) ||
-      !(o.resid_tol >= 0.0) || (o.tie_rule != 0 && o.tie_rule != 1) || o.tail_max_n < 1 ||
+      !(o.resid_tol >= 0.0) || (o.tie_rule != 0 && o.tie_rule != 1) || o.tail_max_n < 1 || o.tail_max_nnz < 1 ||
       o.barrier_timeout_ms < 1 || o.max_batch < 1 || o.max_inflight < 1 || o.max_inflight > 4)
     return FIEDLER_EINVAL;
   fiedler_plan *p = new (std::nothrow) fiedler_plan();

@@ -103,6 +103,7 @@ FZD void best_set(Best &b, uint64_t wk, int u, int v) {
 // per kernel
 constexpr int kShSort = 2048;  // u64 words of the raw buffer (16 KB)
 constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one thread
+constexpr int kHeavyDeg = 32;  // rows of at least this degree are processed by a whole warp
 
 FZD uint64_t *sh_raw() {
   __shared__ uint64_t raw[kShSort];
@@ -227,6 +228,14 @@ FZD void block_dsum(double (&v)[K]) {
 #pragma unroll
   for (int k = 0; k < K; k++) v[k] = sh[k];
   __syncthreads();
+}
+
+// warp sum of one value by a fixed xor tree; result in every lane
+template <class V>
+FZD V warp_sum(V v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // FP64 warp sum of K values by a fixed xor tree; result in every lane
@@ -605,16 +614,22 @@ struct Eng {
   };
   FZD static W wof(const Level *L) { return W{L->w64, L->w32}; }
 
-  FZD bool elig(int n) const { return GRID ? (n > S->opt.tail_max_n) : (n <= S->opt.tail_max_n); }
+  // Small levels run in the one-block engine, large ones in the grid-wide
+  // engine.  n and nnz never grow from a level to the next, so once a level
+  // is small every coarser level is too.
+  FZD static bool tiny(int n, int nnz) { return n <= kTinyN && nnz <= kTinyNnz; }
+  FZD bool small(int n, int nnz) const {
+    return tiny(n, nnz) || (n <= S->opt.tail_max_n && nnz <= S->opt.tail_max_nnz);
+  }
+  FZD bool elig(int n, int nnz) const { return GRID ? !small(n, nnz) : small(n, nnz); }
   // Value type of a level's solve weights and iterates: T, except that the
-  // FP32 form keeps levels of at most kTinyN vertices in FP64.  Those levels
-  // are latency-bound (one warp smooths them), so FP64 costs next to nothing
-  // there, and their power-iteration stop decisions set the coarse start
-  // vector that the whole cascade refines: one iteration more or less on a
-  // 51-vertex level moves the final lambda2 of a 2048 x 1536 grid by 4e-5.
-  // In FP64 those decisions, and the tiny levels' vectors, are the FP64
-  // form's own.
-  FZD static bool vdbl(int n) { return sizeof(T) == 8 || n <= kTinyN; }
+  // FP32 form keeps tiny levels in FP64.  Those levels are latency-bound (one
+  // warp smooths them), so FP64 costs next to nothing there, and their
+  // power-iteration stop decisions set the coarse start vector that the whole
+  // cascade refines: one iteration more or less on a 51-vertex level moves
+  // the final lambda2 of a 2048 x 1536 grid by 4e-5.  In FP64 those
+  // decisions, and the tiny levels' vectors, are the FP64 form's own.
+  FZD static bool vdbl(int n, int nnz) { return sizeof(T) == 8 || tiny(n, nnz); }
 
   FZD int wl_read(int slot) const { return *(volatile int *)&S->wl_cnt[slot]; }
 
@@ -863,7 +878,7 @@ struct Eng {
       return;
     }
     const int ncol = *(volatile int *)&S->col_max + 1;
-    if (ncol > kMaxColors) fail(ST_ENOTSUP);
+    if (2 * ncol > kMaxColors) fail(ST_ENOTSUP);  // the reorder buckets (colour, heavy)
     if (lead()) {
       Level *L = &S->lv[l];
       L->ncolors = ncol;
@@ -884,18 +899,23 @@ struct Eng {
   }
 
   // ---- colour-order copy of the level for the solve phase -------------------
+  // Solve order: colour classes in ascending order; within a class the light
+  // rows (degree < kHeavyDeg) first, then the heavy rows, each group in
+  // ascending vertex order.  Bucket b = 2 * colour + heavy; colstart[b] is the
+  // first solve position of bucket b (2C + 1 entries).
   FZD bool reorder(int l) {
     cur_level = l;
     Level *L = &S->lv[l];
-    const int n = L->n, nnz = L->nnz, C = L->ncolors;
+    const int n = L->n, nnz = L->nnz, C = 2 * L->ncolors;
     const int *rp = L->rowptr, *ci = L->col, *color = L->color;
+    auto bucket = [&](int v) { return 2 * color[v] + (rp[v + 1] - rp[v] >= kHeavyDeg ? 1 : 0); };
     int *hist = (int *)salloc(4ull * C * nb);
     int *perm = (int *)aalloc(4ull * n);
     int *iperm = (int *)aalloc(4ull * n);
     int *colstart = (int *)aalloc(4ull * (C + 1));
     int *srp = (int *)aalloc(4ull * (n + 1));
     int *scol = (int *)aalloc(4ull * (nnz > 0 ? nnz : 1));
-    const bool vd = vdbl(n);
+    const bool vd = vdbl(n, nnz);
     const unsigned long long vsz = vd ? 8ull : sizeof(T);
     void *sw = aalloc(vsz * (unsigned long long)(nnz > 0 ? nnz : 1));
     void *x = aalloc(vsz * (unsigned long long)n);
@@ -909,7 +929,7 @@ struct Eng {
     chunk(n, lo, hi);
     for (int c = threadIdx.x; c < C; c += blockDim.x) sh_cnt[c] = 0;
     __syncthreads();
-    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) atomicAdd(&sh_cnt[color[v]], 1);
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) atomicAdd(&sh_cnt[bucket(v)], 1);
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += blockDim.x) hist[(size_t)c * nb + bid] = sh_cnt[c];
     if (!sync()) return false;
@@ -938,7 +958,7 @@ struct Eng {
     if (C <= 64) {
       for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
         const int v = t0 + threadIdx.x;
-        const int cv = v < hi ? color[v] : -1;
+        const int cv = v < hi ? bucket(v) : -1;
         for (int k = threadIdx.x; k < nw * 64; k += blockDim.x) wc[k >> 6][k & 63] = 0;
         __syncthreads();
         const unsigned peers = __match_any_sync(0xffffffffu, cv);
@@ -966,7 +986,7 @@ struct Eng {
     } else {
       for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
         const int v = t0 + threadIdx.x;
-        const int cv = v < hi ? color[v] : -1;
+        const int cv = v < hi ? bucket(v) : -1;
         for (int c = 0; c < C; c++) {
           if (!__syncthreads_or(cv == c)) continue;
           int tot;
@@ -1532,7 +1552,7 @@ struct Eng {
     }
     double acc[2] = {0.0, 0.0};
     const uint64_t seed = S->opt.seed;
-    const bool vd = vdbl(n);
+    const bool vd = vdbl(n, L->nnz);
     for (int i = tid; i < n; i += nthr) {
       const double v = vd ? uniform01(seed, (uint64_t)i) : (double)(T)uniform01(seed, (uint64_t)i);
       if (vd) ((double *)L->x)[iperm[i]] = v;
@@ -1549,7 +1569,7 @@ struct Eng {
 
   // ---- A8: prolongation y^j = I^T y^{j+1} ----------------------------------
   FZD bool prolong(int l) {
-    const bool vf = vdbl(S->lv[l].n), vc = vdbl(S->lv[l + 1].n);
+    const bool vf = vdbl(S->lv[l].n, S->lv[l].nnz), vc = vdbl(S->lv[l + 1].n, S->lv[l + 1].nnz);
     if (vf) return prolong_v<double, double>(l);
     if (vc) return prolong_v<T, double>(l);
     return prolong_v<T, T>(l);
@@ -1582,9 +1602,17 @@ struct Eng {
 
   // ---- A9 + A10: Gauss-Seidel sweeps, then shifted power iteration ----------
   FZD bool smooth(int l, int kmax, double mu, double s, int gs_phase) {
-    const int n = S->lv[l].n;
-    if (!GRID && n <= kTinyN) return smooth_warp<double>(l, kmax, mu, s, gs_phase);
-    if (vdbl(n)) return smooth_v<double>(l, kmax, mu, s, gs_phase);
+    const int n = S->lv[l].n, nnz = S->lv[l].nnz;
+    if (GRID) {
+      // tiny levels, the FP64-valued ones of the FP32 form, are always small
+      if (vdbl(n, nnz) && sizeof(T) != 8) {
+        fail(ST_ENOTSUP);
+        return false;
+      }
+      return smooth_v<T>(l, kmax, mu, s, gs_phase);
+    }
+    if (tiny(n, nnz)) return smooth_warp<double>(l, kmax, mu, s, gs_phase);
+    if (vdbl(n, nnz)) return smooth_v<double>(l, kmax, mu, s, gs_phase);
     return smooth_v<T>(l, kmax, mu, s, gs_phase);
   }
 
@@ -1593,6 +1621,7 @@ struct Eng {
     Level *L = &S->lv[l];
     const int n = L->n, nnz = L->nnz, C = L->ncolors;
     const int *srp = L->srowptr, *scol = L->scol, *cst = L->colstart;
+    const int lane = threadIdx.x & 31, gw = tid >> 5, nwarp = nthr >> 5;
     const V *sw = (const V *)L->sw;
     V *A = (V *)L->x, *B = (V *)L->y;
     const double g = S->opt.guard;
@@ -1610,8 +1639,8 @@ struct Eng {
     for (int k = 0; k < nsweeps; k++) {
       double acc[2] = {0.0, 0.0};
       for (int c = 0; c < C; c++) {
-        const int cs = cst[c], ce = cst[c + 1];
-        for (int i = cs + tid; i < ce; i += nthr) {
+        const int cs = cst[2 * c], hs = cst[2 * c + 1], ce = cst[2 * c + 2];
+        for (int i = cs + tid; i < hs; i += nthr) {
           V num = (V)0, dsum = (V)0;
           const int e1 = srp[i + 1];
           for (int e = srp[i]; e < e1; e++) {
@@ -1625,6 +1654,26 @@ struct Eng {
           B[i] = xi;
           acc[0] += (double)xi;
           acc[1] += (double)xi * (double)xi;
+        }
+        for (int i = hs + gw; i < ce; i += nwarp) {  // heavy rows: one warp each
+          V num = (V)0, dsum = (V)0;
+          const int e1 = srp[i + 1];
+#pragma unroll 4
+          for (int e = srp[i] + lane; e < e1; e += 32) {
+            const int j = scol[e];
+            const V wv = sw[e];
+            const V xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
+            num += wv * xj;
+            dsum += wv;
+          }
+          num = warp_sum(num);
+          dsum = warp_sum(dsum);
+          const V xi = num / dsum;
+          if (lane == 0) {
+            B[i] = xi;
+            acc[0] += (double)xi;
+            acc[1] += (double)xi * (double)xi;
+          }
         }
         if (c + 1 < C && !sync()) return false;
       }
@@ -1659,11 +1708,7 @@ struct Eng {
     for (int it = 1; it <= kmax; it++) {
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
       double acr[2] = {0.0, 0.0};
-      for (int i = tid; i < n; i += nthr) {
-        const V xi = A[i];
-        V lx = (V)0;
-        const int e1 = srp[i + 1];
-        for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
+      auto row = [&](int i, V xi, V lx) {
         const V xh = (xi - muT) * sT;
         const V yi = sigT * xh - sT * lx;
         B[i] = yi;
@@ -1676,6 +1721,25 @@ struct Eng {
           const double ld = (double)sT * (double)lx;
           acr[0] += ld * ld;
           acr[1] += xd * ld;
+        }
+      };
+      for (int c = 0; c < C; c++) {
+        const int cs = cst[2 * c], hs = cst[2 * c + 1], ce = cst[2 * c + 2];
+        for (int i = cs + tid; i < hs; i += nthr) {
+          const V xi = A[i];
+          V lx = (V)0;
+          const int e1 = srp[i + 1];
+          for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
+          row(i, xi, lx);
+        }
+        for (int i = hs + gw; i < ce; i += nwarp) {
+          const V xi = A[i];
+          V lx = (V)0;
+          const int e1 = srp[i + 1];
+#pragma unroll 4
+          for (int e = srp[i] + lane; e < e1; e += 32) lx += sw[e] * (xi - A[scol[e]]);
+          lx = warp_sum(lx);
+          if (lane == 0) row(i, xi, lx);
         }
       }
       if (!grid_dsum<4>(acc)) return false;
@@ -1724,7 +1788,7 @@ struct Eng {
   }
 
   // The same Gauss-Seidel sweeps and power iteration for tiny levels
-  // (n <= kTinyN, one-block kernel only): warp 0 runs them alone, with warp
+  // (tiny levels, one-block kernel only): warp 0 runs them alone, with warp
   // syncs between colour passes and warp-shuffle FP64 sums, while the other
   // warps wait at one block barrier.  Identical arithmetic per row; only the
   // order of the FP64 sums differs from smooth().
@@ -1747,8 +1811,8 @@ struct Eng {
         double acc[2] = {0.0, 0.0};
         const V muT = (V)mu, sT = (V)s;
         for (int c = 0; c < C; c++) {
-          const int cs = cst[c], ce = cst[c + 1];
-          for (int i = cs + lane; i < ce; i += 32) {
+          const int cs = cst[2 * c], hs = cst[2 * c + 1], ce = cst[2 * c + 2];
+          for (int i = cs + lane; i < hs; i += 32) {
             V num = (V)0, dsum = (V)0;
             const int e1 = srp[i + 1];
             for (int e = srp[i]; e < e1; e++) {
@@ -1762,6 +1826,26 @@ struct Eng {
             B[i] = xi;
             acc[0] += (double)xi;
             acc[1] += (double)xi * (double)xi;
+          }
+          for (int i = hs; i < ce; i++) {  // heavy rows: the warp together
+            V num = (V)0, dsum = (V)0;
+            const int e1 = srp[i + 1];
+#pragma unroll 4
+          for (int e = srp[i] + lane; e < e1; e += 32) {
+              const int j = scol[e];
+              const V wv = sw[e];
+              const V xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
+              num += wv * xj;
+              dsum += wv;
+            }
+            num = warp_sum(num);
+            dsum = warp_sum(dsum);
+            const V xi = num / dsum;
+            if (lane == 0) {
+              B[i] = xi;
+              acc[0] += (double)xi;
+              acc[1] += (double)xi * (double)xi;
+            }
           }
           __syncwarp();
         }
@@ -1794,11 +1878,7 @@ struct Eng {
       for (int it = 1; it <= kmax; it++) {
         double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         const V muT = (V)mu, sT = (V)s, sigT = (V)sigma;
-        for (int i = lane; i < n; i += 32) {
-          const V xi = A[i];
-          V lx = (V)0;
-          const int e1 = srp[i + 1];
-          for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
+        auto row = [&](int i, V xi, V lx) {
           const V xh = (xi - muT) * sT;
           const V yi = sigT * xh - sT * lx;
           B[i] = yi;
@@ -1811,6 +1891,25 @@ struct Eng {
             const double ld = (double)sT * (double)lx;
             acc[4] += ld * ld;
             acc[5] += xd * ld;
+          }
+        };
+        for (int c = 0; c < C; c++) {
+          const int cs = cst[2 * c], hs = cst[2 * c + 1], ce = cst[2 * c + 2];
+          for (int i = cs + lane; i < hs; i += 32) {
+            const V xi = A[i];
+            V lx = (V)0;
+            const int e1 = srp[i + 1];
+            for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
+            row(i, xi, lx);
+          }
+          for (int i = hs; i < ce; i++) {
+            const V xi = A[i];
+            V lx = (V)0;
+            const int e1 = srp[i + 1];
+#pragma unroll 4
+          for (int e = srp[i] + lane; e < e1; e += 32) lx += sw[e] * (xi - A[scol[e]]);
+            lx = warp_sum(lx);
+            if (lane == 0) row(i, xi, lx);
           }
         }
         __syncwarp();
@@ -1858,7 +1957,14 @@ struct Eng {
   }
 
   // ---- A11: Rayleigh quotient, residual, orthogonality, sign, output --------
-  FZD bool finalize() { return vdbl(S->lv[0].n) ? finalize_v<double>() : finalize_v<T>(); }
+  FZD bool finalize() {
+    const int n = S->lv[0].n, nnz = S->lv[0].nnz;
+    if (GRID && vdbl(n, nnz) && sizeof(T) != 8) {  // see smooth()
+      fail(ST_ENOTSUP);
+      return false;
+    }
+    return (!GRID && vdbl(n, nnz)) ? finalize_v<double>() : finalize_v<T>();
+  }
 
   template <class V>
   FZD bool finalize_v() {
@@ -1876,22 +1982,45 @@ struct Eng {
     // by s and s^2 at the end.
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     IRed big{0, 0, LLONG_MIN};
-    for (int k = tid; k < n; k += nthr) {
-      const V xi = A[k];
-      V lx = (V)0, num = (V)0;
-      const int e1 = srp[k + 1];
-      for (int e = srp[k]; e < e1; e++) {
-        const V dl = xi - A[scol[e]];
-        const V wd = sw[e] * dl;
-        lx += wd;
-        num += wd * dl;
-      }
+    auto row = [&](V xi, V lx, V num) {
       const double xk = ((double)xi - mu) * s;
       acc[0] += xk * xk;
       acc[1] += xk;
       acc[2] += (double)num;
       acc[3] += (double)lx * (double)lx;
       big.mx = max(big.mx, (long long)__double_as_longlong(fabs(xk)));
+    };
+    const int *cst = L->colstart, C = L->ncolors;
+    const int lane = threadIdx.x & 31, gw = tid >> 5, nwarp = nthr >> 5;
+    for (int c = 0; c < C; c++) {
+      const int cs = cst[2 * c], hs = cst[2 * c + 1], ce = cst[2 * c + 2];
+      for (int k = cs + tid; k < hs; k += nthr) {
+        const V xi = A[k];
+        V lx = (V)0, num = (V)0;
+        const int e1 = srp[k + 1];
+        for (int e = srp[k]; e < e1; e++) {
+          const V dl = xi - A[scol[e]];
+          const V wd = sw[e] * dl;
+          lx += wd;
+          num += wd * dl;
+        }
+        row(xi, lx, num);
+      }
+      for (int k = hs + gw; k < ce; k += nwarp) {  // heavy rows: one warp each
+        const V xi = A[k];
+        V lx = (V)0, num = (V)0;
+        const int e1 = srp[k + 1];
+#pragma unroll 4
+        for (int e = srp[k] + lane; e < e1; e += 32) {
+          const V dl = xi - A[scol[e]];
+          const V wd = sw[e] * dl;
+          lx += wd;
+          num += wd * dl;
+        }
+        lx = warp_sum(lx);
+        num = warp_sum(num);
+        if (lane == 0) row(xi, lx, num);
+      }
     }
     if (!grid_dsum<4>(acc)) return false;
     acc[2] *= s * s;
@@ -1940,7 +2069,7 @@ struct Eng {
     if (status() != 0) return false;
     if (mode != 2) {
       if (nlevels == 0) {
-        if (!elig(S->n0)) return true;
+        if (!elig(S->n0, S->nnz0)) return true;
         if (!ingest()) return false;
         nlevels = 1;
         persist();
@@ -1948,7 +2077,7 @@ struct Eng {
       while (!setup_done) {
         const int l = nlevels - 1;
         const int n = S->lv[l].n;
-        if (!elig(n)) return true;
+        if (!elig(n, S->lv[l].nnz)) return true;
         soff = 0;  // the level's scratch: colouring, matching, Galerkin
         if (!jp_start(l)) return false;
         bool last = n <= S->opt.coarse_max_n || nlevels >= S->opt.max_levels;
@@ -1975,7 +2104,7 @@ struct Eng {
     if (mode == 0) return true;
     if (!setup_done) return true;
     if (!coarsest_solved) {
-      if (!elig(S->lv[coarsest].n)) return true;
+      if (!elig(S->lv[coarsest].n, S->lv[coarsest].nnz)) return true;
       if (!coarsest_solve(coarsest)) return false;
       coarsest_solved = 1;
       solved = coarsest;
@@ -1983,7 +2112,7 @@ struct Eng {
     }
     while (solved > 0) {
       const int l = solved - 1;
-      if (!elig(S->lv[l].n)) return true;
+      if (!elig(S->lv[l].n, S->lv[l].nnz)) return true;
       if (!prolong(l)) return false;
       solved = l;
       persist();

@@ -12,7 +12,10 @@ constexpr int kMaxBlocks = 2048;   // grid-wide kernel blocks (partials buffer s
 constexpr int kMaxColors = 1024;   // colour classes per level supported by the reorder
 constexpr int kCtaThreads = 512;   // one-block kernel
 constexpr int kGridThreads = 512;  // grid-wide kernel block size
-constexpr int kTinyN = 256;        // levels up to this size: one warp smooths them (FP64 values)
+// tiny levels (n <= kTinyN and nnz <= kTinyNnz): always in the one-block
+// engine, smoothed by one warp, values in FP64 in both forms
+constexpr int kTinyN = 256;
+constexpr int kTinyNnz = 4096;
 
 enum Phase {
   PH_INGEST = 0, PH_COLOR, PH_REORDER, PH_MATCH, PH_AGG, PH_GALERKIN,
@@ -35,6 +38,7 @@ struct Opts {
   int tie_rule;
   int validate;
   int tail_max_n;
+  int tail_max_nnz;
   int fault_inject;
   double stall_ratio;
   double pi_cos_tol;

@@ -4,9 +4,9 @@
 
 namespace fz {
 struct KernelSet {
-  const void *grid_setup;  // cooperative, kGridThreads per block: setup of levels with n > tail_max_n
-  const void *grid_solve;  // cooperative, kGridThreads per block: solve of levels with n > tail_max_n
-  const void *cta;         // one block of kCtaThreads: everything on levels with n <= tail_max_n
+  const void *grid_setup;  // cooperative, kGridThreads per block: setup of the large levels
+  const void *grid_solve;  // cooperative, kGridThreads per block: solve of the large levels
+  const void *cta;         // one block of kCtaThreads: everything on the small levels
   const void *batch;       // persistent blocks of kCtaThreads, one graph at a time each
   const char *names[4];    // profile slots: grid_setup, cta, grid_solve, batch
 };

@@ -127,6 +127,7 @@ extern "C" fiedler_status fiedler_solve_noalloc(const fiedler_options *opts, con
   so.tie_rule = o.tie_rule;
   so.validate = o.validate;
   so.tail_max_n = INT_MAX;  // every level in the one-block engine
+  so.tail_max_nnz = INT_MAX;
   so.fault_inject = 0;
   so.stall_ratio = o.stall_ratio;
   so.pi_cos_tol = o.pi_cos_tol;

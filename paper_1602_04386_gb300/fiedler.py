@@ -63,6 +63,7 @@ class fiedler_options(C.Structure):
         ("seed", C.c_uint64),
         ("validate", C.c_int),
         ("tail_max_n", C.c_int),
+        ("tail_max_nnz", C.c_int),
         ("barrier_timeout_ms", C.c_int),
         ("fault_inject", C.c_int),
         ("hbm_budget_bytes", C.c_size_t),

@@ -2,7 +2,7 @@
 
 A graph's result must not depend on the batch it runs in: batched results
 are compared bit for bit with the same graph solved alone (one-block engine:
-tail_max_n >= n), alone and in mixes, through fiedler_solve_batch and the
+tail_max_n >= n and tail_max_nnz >= nnz), alone and in mixes, through fiedler_solve_batch and the
 ticket queue, including tickets admitted while others are on the GPU.  A
 sample is also checked against the oracle (hierarchy bit for bit, lambda_2
 to 1e-10 in FP64, 1e-5 in FP32)."""
@@ -37,7 +37,7 @@ def mixed_grids(k, seed=0):
 
 
 def alone(g, precision):
-    with fiedler.Plan(precision=precision, tail_max_n=1 << 30) as p:
+    with fiedler.Plan(precision=precision, tail_max_n=1 << 30, tail_max_nnz=1 << 30) as p:
         return p.solve(g)
 
 
@@ -61,7 +61,7 @@ def test_batch_against_oracle_sample():
     with fiedler.Plan(precision=fiedler.FIEDLER_FP64) as p:
         res = p.solve_batch(gs)
     for g, r in zip(gs[:3], res[:3]):
-        with fiedler.Plan(precision=fiedler.FIEDLER_FP64, tail_max_n=1 << 30) as q:
+        with fiedler.Plan(precision=fiedler.FIEDLER_FP64, tail_max_n=1 << 30, tail_max_nnz=1 << 30) as q:
             a = q.solve(g)
             counts = [q.level_info(l).pi_iters for l in range(q.num_levels)]
         ref = oracle.solve(g, forced_pi=counts)

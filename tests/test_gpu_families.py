@@ -62,7 +62,7 @@ def test_batch_mix_equals_single_solves():
     with fiedler.Plan() as p:
         res = p.solve_batch(gs)
     for g, r in zip(gs, res):
-        with fiedler.Plan(tail_max_n=1 << 30) as q:
+        with fiedler.Plan(tail_max_n=1 << 30, tail_max_nnz=1 << 30) as q:
             a = q.solve(g)
         assert r.status == a.status == fiedler.FIEDLER_OK
         assert r.lambda2 == a.lambda2 and np.array_equal(r.x, a.x)

@@ -105,10 +105,10 @@ def test_weighted_grid_grid_wide_path(m, k, precision, tol):
     compare(g, precision, tol)
 
 
-@pytest.mark.parametrize("tail", [64, 1000, 1 << 30])
-def test_tail_threshold_does_not_change_results(tail):
+@pytest.mark.parametrize("tail,tail_nnz", [(64, 32768), (1000, 32768), (1 << 30, 1 << 30), (1 << 30, 5000)])
+def test_tail_threshold_does_not_change_results(tail, tail_nnz):
     g = inputs.grid(120, 90, "uniform", seed=5)
-    compare(g, FP64, 1e-10, 1e-8, tail_max_n=tail)
+    compare(g, FP64, 1e-10, 1e-8, tail_max_n=tail, tail_max_nnz=tail_nnz)
 
 
 def test_host_inputs_equal_device_inputs():

@@ -44,7 +44,7 @@ def test_noalloc_matches_plan_solve_twice(precision, graph):
     g = {"grid64x48": lambda: inputs.grid(64, 48, "unit"),
          "grid150x101w": lambda: inputs.grid(150, 101, "uniform", seed=7)}[graph]()
     lam_tol, x_tol = TOL[precision]
-    with fiedler.Plan(precision=precision, tail_max_n=1 << 30) as p:
+    with fiedler.Plan(precision=precision, tail_max_n=1 << 30, tail_max_nnz=1 << 30) as p:
         ref = p.solve(g)
     assert ref.status == fiedler.FIEDLER_OK
     stream = torch.cuda.current_stream().cuda_stream
