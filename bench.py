@@ -193,6 +193,13 @@ def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15):
         return e0.elapsed_time(e1), wall
 
     plan = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP32_FP64RED)
+    # autotuner: block size per graph chosen on every 16th graph of the batch
+    tsample = (fiedler.fiedler_graph * len(range(0, count, 16)))()
+    for k, i in enumerate(range(0, count, 16)):
+        tsample[k] = garr[i]
+    st, tuning = fiedler.fiedler_plan_autotune(plan.h, tsample)
+    if st != fiedler.FIEDLER_OK:
+        raise fiedler.FiedlerError(st, "fiedler_plan_autotune")
     for _ in range(warmup):
         run_batch(plan)
     plan.set_profiling(True)
@@ -202,6 +209,7 @@ def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15):
         ms.append(t)
         walls.append(wall)
         pr = plan.profile()
+        pr_name = pr.kernel_name[3].decode()
         kms += pr.kernel_ms[3]
         kbytes += pr.kernel_bytes[3]
         launches += int(pr.kernel_launches)
@@ -252,9 +260,11 @@ def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15):
     return {
         "workload": batch_name(count), "graphs": count, "vertices": int(sum(g.n for g in graphs)), "nnz": nnz,
         "form": "FP32 values/matvec, FP64 reductions; one persistent launch per call",
+        "autotune": {"batch_threads": tuning.batch_threads, "sample_ms_512_256_128": [round(x, 2) for x in tuning.batch_ms],
+                     "sample": f"every 16th graph ({len(tsample)})"},
         "solves_per_s": count / (ms_step / 1e3), "ms_per_batch": ms_step, "wall_ms_per_batch": 1e3 * statistics.mean(walls),
         "statuses_ok": int((st32 == 0).sum()),
-        "kernel": "fz_batch_f32", "kernel_ms": kms / steps, "gpu_launches_per_batch": launches / steps,
+        "kernel": pr_name, "kernel_ms": kms / steps, "gpu_launches_per_batch": launches / steps,
         "kernel_algorithmic_gbs": kgbs, "kernel_frac": (kgbs / peak) if kgbs else None, "peak_kind": f"of {peak_kind}",
         "fp64_batched_solves_per_s": count / (t64b / 1e3),
         "fp64_plain_solves_per_s": len(sample) / (t64 / 1e3) / scale,
@@ -263,6 +273,122 @@ def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15):
                                           "rmat": agree(rel[fam == 1])},
         "lambda2_rel_err_vs_fp64_batched": agree(relb),
         "fp64_batched_statuses_ok": int((st64b == 0).sum()),
+    }
+
+
+SERVE = dict(rate=2000.0, seconds=3.0, pool=24, nmin=1e3, nmax=2e6, seed=inputs.BASE_SEED + 5)
+
+
+def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"]):
+    """The serving form: a Poisson stream of requests at `rate` per second for
+    `seconds`, each a graph drawn uniformly from the pool (device-resident
+    inputs, copied by fiedler_batch_submit), submitted at its arrival time and
+    polled by a second thread; the plan's continuous batching admits tickets by
+    their device-memory footprint.  When the queue budget is used up the
+    submitter waits and retries (back-pressure), so a request's latency is
+    taken from its scheduled arrival to the poll that returns its result.
+    Throughput is completions over first arrival to last completion."""
+    import threading
+    import torch
+    from paper_1602_04386_gb300 import fiedler
+    nreq = int(rate * seconds)
+    u = inputs.uniform01(seed, np.arange(2 * nreq))
+    t_arr = np.cumsum(-np.log1p(-u[:nreq]) / rate)
+    pick = np.minimum((u[nreq:] * len(pool)).astype(np.int64), len(pool) - 1)
+    dgs = [fiedler.device_graph(g, dev) for g in pool]
+    plan = fiedler.Plan(stream=stream.cuda_stream, max_batch=256, hbm_budget_bytes=160 << 30,
+                        queue_budget_bytes=24 << 30)
+    tsample = (fiedler.fiedler_graph * len(dgs))()
+    for k, (gs, _) in enumerate(dgs):
+        tsample[k] = gs
+    st, tuning = fiedler.fiedler_plan_autotune(plan.h, tsample)
+    if st != fiedler.FIEDLER_OK:
+        raise fiedler.FiedlerError(st, "fiedler_plan_autotune")
+    plan_slots = torch.cuda.get_device_properties(dev).multi_processor_count * (512 // tuning.batch_threads)
+    tickets = []
+    lat = np.full(nreq, np.nan)
+    stats_st = np.zeros(nreq, np.int64)
+    state = {"bad": 0, "t_last": 0.0, "stop": False, "err": None}
+    cond = threading.Condition()
+    t0 = 0.0
+
+    def poller():
+        k = 0
+        while k < nreq and not state["stop"]:
+            with cond:
+                while k >= len(tickets) and not state["stop"]:
+                    cond.wait(timeout=1.0)
+                if state["stop"]:
+                    return
+                t = tickets[k]
+            r = fiedler.fiedler_result()
+            st = fiedler.fiedler_poll(plan.h, t, 1000, r)
+            if st == fiedler.FIEDLER_EAGAIN:
+                continue  # not yet: poll the same ticket again (bounded waits, stop flag checked)
+            now = time.perf_counter()
+            lat[k] = now - t0 - t_arr[k]
+            stats_st[k] = st
+            state["bad"] += st != fiedler.FIEDLER_OK
+            state["t_last"] = now
+            k += 1
+
+    try:
+        # warm-up: one request of each pool graph, one at a time
+        for gs, _ in dgs:
+            st, t = fiedler.fiedler_batch_submit(plan.h, gs)
+            if st != fiedler.FIEDLER_OK:
+                raise fiedler.FiedlerError(st, "fiedler_batch_submit")
+            while fiedler.fiedler_poll(plan.h, t, 1000, fiedler.fiedler_result()) == fiedler.FIEDLER_EAGAIN:
+                pass
+        base = plan.serving_stats()
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        retries = 0
+        for i in range(nreq):
+            now = time.perf_counter() - t0
+            if t_arr[i] > now:
+                time.sleep(t_arr[i] - now)
+            while True:
+                st, t = fiedler.fiedler_batch_submit(plan.h, dgs[pick[i]][0])
+                if st != fiedler.FIEDLER_EAGAIN:
+                    break
+                retries += 1
+                time.sleep(2e-4)
+            if st != fiedler.FIEDLER_OK:
+                raise fiedler.FiedlerError(st, "fiedler_batch_submit")
+            with cond:
+                tickets.append(t)
+                cond.notify()
+        t_sub = time.perf_counter() - t0
+        th.join(timeout=600.0)
+        if th.is_alive():
+            raise RuntimeError("serving leg: completions did not arrive within 600 s")
+        ss = plan.serving_stats()
+    finally:
+        state["stop"] = True
+        with cond:
+            cond.notify_all()
+        plan.close()
+    wall = state["t_last"] - t0
+    sizes = np.array([pool[i].n for i in pick])
+    return {
+        "workload": f"Poisson {rate:g} req/s for {seconds:g} s; kNN mixture graphs, {len(pool)} sizes log-spaced "
+                    f"{SERVE['nmin']:g}..{SERVE['nmax']:g} points (largest component kept), seed {seed}",
+        "requests": nreq, "completed_ok": int(nreq - state["bad"]), "submit_span_s": t_sub,
+        "submit_retries": retries, "wall_s": wall, "solves_per_s": nreq / wall,
+        "p50_ms": 1e3 * float(np.nanpercentile(lat, 50)), "p99_ms": 1e3 * float(np.nanpercentile(lat, 99)),
+        "latency": "scheduled arrival to result, client side (includes waiting for queue room)",
+        "library_p50_ms": ss.p50_ms, "library_p99_ms": ss.p99_ms,
+        "batches": int(ss.batches - base.batches), "mean_batch": ss.mean_batch,
+        "peak_inflight_gb": ss.peak_inflight_bytes / 1e9,
+        "kernel_launches": int(ss.launches - base.launches), "block_seconds": ss.block_seconds - base.block_seconds,
+        "mean_unfinished": ss.mean_inflight, "mean_blocks_alive": ss.mean_blocks,
+        "sm_occupancy_est": (ss.block_seconds - base.block_seconds) / wall / max(1, plan_slots),
+        "vertices_mean": float(sizes.mean()), "vertices_p99": float(np.percentile(sizes, 99)),
+        "form": "FP32 values/matvec, FP64 reductions; continuous batching through a persistent kernel",
+        "autotune": {"batch_threads": tuning.batch_threads, "pool_ms_512_256_128": [round(x, 2) for x in tuning.batch_ms]},
+        "statuses": {str(k): int(v) for k, v in zip(*np.unique(stats_st, return_counts=True))},
     }
 
 
@@ -312,6 +438,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp64 / cpu baseline legs (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form leg")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"])
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-form leg")
+    ap.add_argument("--serve-rate", type=float, default=SERVE["rate"])
+    ap.add_argument("--serve-seconds", type=float, default=SERVE["seconds"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.no_extras:
         args.warmup = 3
@@ -321,6 +450,10 @@ def main():
     if not args.no_batch and not args.no_extras:
         # generated before CUDA is initialised (worker processes are spawned anyway)
         batch_graphs = inputs.batch_mix(args.batch_count, seed=BATCH["seed"], procs=min(16, os.cpu_count() or 1))
+    serve_pool = None
+    if not args.no_serve and not args.no_extras:
+        serve_pool = inputs.serving_pool(SERVE["pool"], SERVE["nmin"], SERVE["nmax"], SERVE["seed"],
+                                         procs=min(16, os.cpu_count() or 1))
 
     import torch
     from paper_1602_04386_gb300 import fiedler
@@ -349,6 +482,10 @@ def main():
             raise fiedler.FiedlerError(r.status, "fiedler_solve")
         return r
 
+    # the clock sampler starts before the warm-up, so that nvidia-smi's own
+    # start-up is not inside the timed region
+    clk = ClockSampler(local).__enter__()
+    time.sleep(0.5)
     for _ in range(args.warmup):
         flush.zero_()
         solve_once()
@@ -365,7 +502,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
-    with ClockSampler(local) as clk:
+    if True:
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
@@ -382,6 +519,7 @@ def main():
             ph_ms += np.array([[pr.phase_ms[a][b] for b in range(16)] for a in range(2)])
             ph_bytes += np.array([[pr.phase_bytes[a][b] for b in range(16)] for a in range(2)])
         torch.cuda.synchronize()
+    clk.__exit__()
     if dist is not None:
         dist.barrier()
     wall = time.perf_counter() - t_wall
@@ -417,6 +555,7 @@ def main():
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "flushed between steps (256 MiB write outside the timed events); working set > L2"},
         "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+        "step_ms": [round(t, 3) for t in step_ms],
         "wall_s": wall,
         "lambda2": res.lambda2, "residual": res.residual, "levels": res.levels,
         "spmv_gs_hbm_gbs": spmv_gs_gbs,
@@ -505,6 +644,9 @@ def main():
     if batch_graphs is not None:
         line["batched"] = batched_leg(batch_graphs, stream, dev)
         line["gpu_launches_batched_per_batch"] = line["batched"]["gpu_launches_per_batch"]
+        del batch_graphs
+    if serve_pool is not None:
+        line["serving"] = serving_leg(serve_pool, stream, dev, args.serve_rate, args.serve_seconds)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

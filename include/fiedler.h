@@ -39,7 +39,8 @@ extern "C" {
 
 typedef enum {
   FIEDLER_OK = 0,
-  FIEDLER_EAGAIN = 1,            /* fiedler_poll: the ticket is still in flight */
+  FIEDLER_EAGAIN = 1,            /* fiedler_poll: the ticket is still in flight;
+                                    fiedler_batch_submit: the queue budget is used up */
   FIEDLER_EINVAL = -1,           /* malformed arguments or CSR (see result.bad_index) */
   FIEDLER_ENOMEM = -2,           /* device memory could not be obtained */
   FIEDLER_EDISCONNECTED = -3,    /* the graph is not connected: lambda_2 = 0 is degenerate */
@@ -84,8 +85,13 @@ typedef struct {
   int fault_inject;          /* testing only: 1 = one block skips the first grid barrier, so the
                                 others' bounded wait runs out and the solve reports ETIMEOUT */
   size_t hbm_budget_bytes;   /* serving: device memory the in-flight tickets may hold (0 = 16 GiB) */
-  int max_batch;             /* serving: most tickets per batched launch */
-  int max_inflight;          /* serving: batched launches in flight at once (1..4) */
+  int max_batch;             /* serving: most tickets admitted in one scheduling round */
+  size_t queue_budget_bytes; /* serving: device memory the copied inputs of submitted, not yet
+                                polled tickets may hold (0 = 8 GiB); beyond it fiedler_batch_submit
+                                returns FIEDLER_EAGAIN */
+  int batch_threads;         /* batched and serving forms: threads per graph's block, 512, 256 or
+                                128 (1, 2 or 4 graphs per SM); 0 = 512 until fiedler_plan_autotune
+                                picks one */
 } fiedler_options;
 
 typedef struct {
@@ -121,7 +127,8 @@ typedef struct fiedler_plan fiedler_plan;
  * stall_ratio 0.9, gs_sweeps 2, pi_max_iters 10000, pi_max_iters_coarsest
  * 100000, pi_cos_tol 1e-6, resid_tol 0, hashed ties, seed 20160214,
  * validate 1, tail_max_n 4096, tail_max_nnz 32768, barrier_timeout_ms 5000, fault_inject 0,
- * hbm_budget_bytes 0 (16 GiB), max_batch 1024, max_inflight 2. */
+ * hbm_budget_bytes 0 (16 GiB), max_batch 1024, queue_budget_bytes 0 (8 GiB),
+ * batch_threads 0. */
 void fiedler_options_default(fiedler_options *opts);
 
 /* Creates a plan on the current CUDA device.  opts may be NULL (defaults);
@@ -148,13 +155,21 @@ fiedler_status fiedler_solve(fiedler_plan *plan, const fiedler_graph *graph, fie
 fiedler_status fiedler_solve_batch(fiedler_plan *plan, const fiedler_graph *graphs, int count,
                                    fiedler_result *results);
 
-/* Serving form (continuous batching): fiedler_batch_submit copies the graph
- * (host or device) into plan-owned memory, queues it and returns a ticket at
- * once.  A scheduler thread admits queued tickets into batched launches while
- * the device memory held by in-flight tickets stays within hbm_budget_bytes;
- * up to max_inflight launches run concurrently on their own streams, so
- * tickets that arrive while others are on the GPU start as soon as memory and
- * a launch slot free up.  Thread-safe against fiedler_poll / fiedler_cancel. */
+/* Serving form (continuous batching; a project addition): fiedler_batch_submit
+ * copies the graph (host or device) into plan-owned memory, queues it and
+ * returns a ticket at once; it returns FIEDLER_EAGAIN without queueing when
+ * the copies held by earlier tickets (until they are polled) would exceed
+ * queue_budget_bytes, so the caller can wait for completions and submit again
+ * (back-pressure).  A scheduler thread admits queued tickets while the device
+ * memory of the tickets in flight (state, hierarchy arena, scratch) stays
+ * within hbm_budget_bytes, at most max_batch per round, and publishes them to
+ * a persistent kernel whose resident blocks (one graph each, as in the batched
+ * form, batch_threads per block) take them in order and finish each one
+ * independently: a ticket admitted while others are on the GPU starts as soon
+ * as a block is free, and a finished ticket returns its memory at once.
+ * Thread-safe against fiedler_poll / fiedler_cancel.  While tickets are in
+ * flight the serving kernel may occupy every SM, so a plan's fiedler_solve
+ * should not run at the same time on the same device. */
 fiedler_status fiedler_batch_submit(fiedler_plan *plan, const fiedler_graph *graph, uint64_t *ticket);
 
 /* Waits up to timeout_ms (0 = do not wait, < 0 = wait forever) for a ticket.
@@ -222,10 +237,31 @@ typedef struct {
   double p50_ms, p99_ms, mean_ms;           /* ticket latency, submit to completion */
   double mean_batch;                        /* tickets per batched launch */
   size_t peak_inflight_bytes;               /* most device memory held by in-flight tickets */
+  uint64_t launches;                        /* serving kernel launches */
+  double block_seconds;                     /* device time of the finished tickets' solves, summed */
+  double mean_inflight;                     /* unfinished published tickets, averaged over scheduler rounds */
+  double mean_blocks;                       /* serving blocks alive, averaged the same way */
 } fiedler_serving_stats;
 
 /* Counters of the serving form. */
 fiedler_status fiedler_plan_serving_stats(const fiedler_plan *plan, fiedler_serving_stats *out);
+
+typedef struct {
+  int batch_threads;         /* block size chosen for this plan's batched and served launches */
+  float batch_ms[3];         /* CUDA-event time of the sample batch with 512, 256 and 128
+                                threads per graph (0 = not measured) */
+} fiedler_tuning;
+
+/* Autotuner of the batched form (a project addition; the paper has none):
+ * solves the `count` sample graphs as one batch with each block size (512,
+ * 256 and 128 threads per graph, i.e. 1, 2 and 4 graphs resident per SM),
+ * keeps the fastest for every later fiedler_solve_batch and serving launch of
+ * this plan, and reports the timings.  Results depend on the block size only
+ * through the rounding of block-wide sums, so a graph gives the same result in
+ * any batch of a tuned plan; the sample results are discarded.  Returns EINVAL
+ * for an empty sample or a plan created with a fixed batch_threads. */
+fiedler_status fiedler_plan_autotune(fiedler_plan *plan, const fiedler_graph *graphs, int count,
+                                     fiedler_tuning *out);
 
 /* 1: record CUDA events around every kernel of the following solves. */
 fiedler_status fiedler_plan_set_profiling(fiedler_plan *plan, int on);

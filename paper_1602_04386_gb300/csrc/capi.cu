@@ -9,10 +9,12 @@
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -33,11 +35,16 @@ namespace {
 struct Ticket {
   uint64_t id;
   int64_t n, nnz;
+  char *buf = nullptr;  // one pool allocation: rowptr | col | w | x
+  size_t bytes = 0;     // its size (charged to the queue budget until polled)
   int32_t *rowptr = nullptr, *col = nullptr;
   void *w = nullptr;
   int w_dtype = 0;
   double *x = nullptr;  // device result vector
   size_t footprint = 0;  // device bytes while in flight (admission)
+  double scale = 1.0;     // arena / scratch estimate factor (doubled on a rerun)
+  char *dwork = nullptr;  // in flight: state | arena | scratch (pool allocation)
+  unsigned long long k = 0;  // position in the serving ring
   std::chrono::steady_clock::time_point t_submit;
   fiedler_result res{};
   fiedler_status st = FIEDLER_EAGAIN;
@@ -89,7 +96,9 @@ struct fiedler_plan {
   int device = 0, sms = 0;
   fz::KernelSet ks[2];      // [0] double, [1] float
   int grid_blocks[2][2];    // [type][setup/solve]
-  int batch_slots[2];       // resident blocks of the batched kernel
+  int batch_slots[2][3];    // resident blocks of each batched kernel variant
+  int serve_slots[2][3];    // and of each serving kernel variant
+  int batch_var = 0;        // variant used by batched and served launches (kBatchThreads)
   State *d_state = nullptr;
   State *h_state = nullptr; // pinned mirror
   fz::IRed *d_ipart = nullptr;
@@ -108,7 +117,30 @@ struct fiedler_plan {
   bool have_result = false;
   fiedler_profile prof;
   BatchCtx bsync;           // fiedler_solve_batch (plan stream)
-  BatchCtx bserve[4];       // serving launches (own streams)
+  // ticket inputs and outputs: a stream-ordered pool on a stream of their own,
+  // so that submit and poll never wait for the device as a whole
+  cudaStream_t io_stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  // serving form: a persistent kernel fed through a ring in device memory
+  fz::ServeRing *d_ring = nullptr;
+  fz::ServeDone *done = nullptr;      // host view of the completion flags (pinned, mapped)
+  fz::ServeDone *done_dev = nullptr;  // device view of the same memory
+  unsigned long long *h_pub = nullptr;  // pinned staging: item pointers of a round, then the tail
+  unsigned long long published = 0;
+  static constexpr unsigned long long kIdleNs = 20000000ull;  // a serving block idle this long leaves
+  struct ServeLaunch {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool running = false;
+    unsigned long long base = 0;  // number of its first block
+    int nb = 0;
+  };
+  std::vector<ServeLaunch> serve;    // launch records (own streams), reused once finished
+  unsigned long long block_next = 0;
+  State *h_stage = nullptr;           // pinned staging of ticket states (max_batch of them)
+  int stage_n = 0;
+  std::deque<Ticket *> live;          // published, not yet finished (ring order)
+  uint64_t n_launches = 0;
   // serving form
   std::mutex exec_mu;       // one solve on the device state at a time
   std::mutex q_mu;
@@ -119,8 +151,11 @@ struct fiedler_plan {
   std::thread worker;
   bool stop = false;
   size_t inflight_bytes = 0, peak_inflight = 0;
+  size_t queued_bytes = 0;  // pool bytes of submitted, not yet polled tickets
   uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, n_batched_tickets = 0;
   std::vector<float> latencies_ms;
+  double block_seconds = 0.0, live_sum = 0.0, alive_sum = 0.0;
+  uint64_t live_rounds = 0;
 };
 
 namespace {
@@ -386,6 +421,10 @@ fiedler_status solve_locked(fiedler_plan *p, const fiedler_graph *g, fiedler_res
 size_t r256(size_t b) { return (b + 255u) & ~(size_t)255u; }
 
 fiedler_status ctx_reserve(BatchCtx &c, size_t dbytes, size_t hbytes) {
+  // grow by half again at least, so that a stream of growing batches
+  // reallocates (and frees pinned host memory) rarely
+  if (c.d_cap < dbytes) dbytes = std::max(dbytes, c.d_cap + c.d_cap / 2);
+  if (c.h_cap < hbytes) hbytes = std::max(hbytes, c.h_cap + c.h_cap / 2);
   if (c.d_cap < dbytes) {
     if (c.d_buf) CK(cudaFreeAsync(c.d_buf, c.stream));
     c.d_buf = nullptr;
@@ -419,7 +458,8 @@ fiedler_status batch_launch(fiedler_plan *p, BatchCtx &c, double arena_scale) {
   std::stable_sort(c.items.begin(), c.items.end(),
                    [](const BatchItem &a, const BatchItem &b) { return a.nnz + a.n > b.nnz + b.n; });
   const int count = (int)c.items.size();
-  const int nslots = std::min(count, p->batch_slots[type]);
+  const int var = p->batch_var;
+  const int nslots = std::min(count, p->batch_slots[type][var]);
   size_t slot = 0, arenas = 0, in_b = 0, x_b = 0;
   for (auto &it : c.items) {
     it.arena_b = r256((size_t)(arena_estimate(it.n, it.nnz, tsz, it.wf64) * arena_scale));
@@ -501,7 +541,7 @@ fiedler_status batch_launch(fiedler_plan *p, BatchCtx &c, double arena_scale) {
   void *args[] = {(void *)&d_states, (void *)&count, (void *)&d_counter, (void *)&d_scratch, (void *)&slot_bytes};
   const bool prof = p->profiling && &c == &p->bsync;
   if (prof) CK(cudaEventRecord(p->ev[8], c.stream));
-  CK(cudaLaunchKernel(p->ks[type].batch, dim3(nslots), dim3(fz::kCtaThreads), args, 0, c.stream));
+  CK(cudaLaunchKernel(p->ks[type].batch_v[var], dim3(nslots), dim3(fz::kBatchThreads[var]), args, 0, c.stream));
   if (prof) CK(cudaEventRecord(p->ev[9], c.stream));
   CK(cudaMemcpyAsync(hs, c.d_buf + c.d_states, sizeof(State) * (size_t)count, cudaMemcpyDeviceToHost, c.stream));
   if (x_b) CK(cudaMemcpyAsync(c.h_buf + c.h_x, c.d_buf + c.d_x, x_b, cudaMemcpyDeviceToHost, c.stream));
@@ -552,7 +592,8 @@ void batch_profile(fiedler_plan *p, BatchCtx &c) {
   fiedler_profile &pr = p->prof;
   const fz::KernelSet &K = p->ks[c.type];
   pr.n_kernels = 4;
-  for (int k = 0; k < 4; k++) pr.kernel_name[k] = K.names[k];
+  for (int k = 0; k < 3; k++) pr.kernel_name[k] = K.names[k];
+  pr.kernel_name[3] = K.batch_names[p->batch_var];
   float km = 0.f;
   cudaEventElapsedTime(&km, p->ev[8], p->ev[9]);
   pr.kernel_ms[3] += km;
@@ -597,145 +638,286 @@ fiedler_status batch_run_sync(fiedler_plan *p, BatchCtx &c) {
   return FIEDLER_OK;
 }
 
-void free_ticket(Ticket *t) {
-  cudaFree(t->rowptr);
-  cudaFree(t->col);
-  cudaFree(t->w);
-  cudaFree(t->x);
+// caller holds q_mu (or is the only thread left)
+void free_ticket(fiedler_plan *p, Ticket *t) {
+  if (t->buf) cudaFreeAsync(t->buf, p->io_stream);  // the ticket's launch has finished
+  p->queued_bytes -= t->bytes;
   delete t;
 }
 
 // ---- serving form: continuous batching -----------------------------------
-// The scheduler admits queued tickets into a batched launch while the device
-// memory of in-flight tickets stays within the budget (a launch always takes
-// at least one ticket when nothing else is in flight), keeps up to
-// max_inflight launches running on their own streams, and completes tickets
-// as their launch's event fires.
-void complete_ctx(fiedler_plan *p, BatchCtx &c) {
-  batch_collect(c);
-  std::vector<BatchItem> rerun;
-  for (auto &it : c.items)
-    if (needs_rerun(it.st)) rerun.push_back(it);
-  if (!rerun.empty()) {  // rare: regrow and run those again, synchronously
-    std::vector<BatchItem> keep = c.items;
-    c.items = rerun;
-    double scale = 2.0;
-    for (int attempt = 0; attempt < 3 && !c.items.empty(); attempt++, scale *= 2.0) {
-      if (batch_launch(p, c, scale) != FIEDLER_OK || cudaEventSynchronize(c.done) != cudaSuccess) break;
-      batch_collect(c);
-      std::vector<BatchItem> again;
-      for (auto &it : c.items)
-        if (needs_rerun(it.st)) again.push_back(it);
-      c.items = again;
-    }
-    for (auto &it : c.items) it.ticket->st = FIEDLER_ENOMEM;
-    c.items = keep;
+// A scheduler thread admits queued tickets while the device memory of the
+// tickets in flight stays within the budget (a ticket is always admitted when
+// nothing else is in flight): each admitted ticket gets one pool allocation
+// holding its solve state, hierarchy arena and scratch, its state header is
+// copied in, and it is published in the serving ring.  The serving kernel's
+// resident blocks (one graph each, as in the batched form) claim published
+// tickets in order and flag each as soon as it is done; the scheduler reads
+// the flags, copies the finished state back and completes the ticket, which
+// returns its memory to the budget at once.  A long solve therefore holds one
+// block, not a launch.  The kernel's blocks leave after an idle spell; the
+// scheduler launches it again whenever published work is waiting and no block
+// is left.
+
+// fills the device-side state header of a ticket (host copy in *h)
+void fill_ticket_state(fiedler_plan *p, Ticket *t, State *h, int type, size_t arena_b, size_t scratch_b) {
+  memset(h, 0, sizeof(State));
+  fill_opts(h->opt, p->opt, type);
+  h->opt.tail_max_n = INT_MAX;  // every level in the one-block engine
+  h->opt.tail_max_nnz = INT_MAX;
+  h->opt.fault_inject = 0;
+  h->bad_index = LLONG_MAX;
+  h->n0 = (int)t->n;
+  h->nnz0 = (int)t->nnz;
+  h->in_rowptr = t->rowptr;
+  h->in_col = t->col;
+  h->in_w = t->w;
+  h->in_w_f64 = t->w_dtype == FIEDLER_W_F64;
+  h->arena = t->dwork + r256(sizeof(State));
+  h->arena_size = arena_b;
+  h->scratch = h->arena + arena_b;
+  h->scratch_size = scratch_b;
+  h->xout = t->x;
+}
+
+void ticket_result(const State *h, Ticket *t) {
+  fiedler_result r{};
+  fiedler_status out = map_status(h->status);
+  if (out == FIEDLER_OK && !h->finalized) out = FIEDLER_ECUDA;
+  if (out == FIEDLER_OK && h->capped) out = FIEDLER_ENOTCONVERGED;
+  r.levels = h->nlevels;
+  r.coarsest_n = h->nlevels > 0 ? h->lv[h->coarsest].n : 0;
+  r.bad_index = h->bad_index == LLONG_MAX ? -1 : h->bad_index;
+  if (out == FIEDLER_OK || out == FIEDLER_ENOTCONVERGED) {
+    r.lambda2 = h->lambda;
+    r.residual = h->residual;
+    r.ortho = h->ortho;
+    r.pi_iters_total = h->pi_total;
+    r.gs_sweeps_total = h->gs_total;
   }
-  const auto now = std::chrono::steady_clock::now();
-  std::lock_guard<std::mutex> lk(p->q_mu);
-  for (auto &it : c.items) {
-    Ticket *t = it.ticket;
-    t->done = true;
-    t->running = false;
-    p->inflight_bytes -= t->footprint;
-    p->n_completed++;
-    p->latencies_ms.push_back(std::chrono::duration<float, std::milli>(now - t->t_submit).count());
-  }
-  c.items.clear();
-  c.busy = false;
-  p->q_cv.notify_all();
+  r.x = t->x;
+  r.x_on_device = 1;
+  r.status = out;
+  t->res = r;
+  t->st = out;
 }
 
 void worker_main(fiedler_plan *p) {
   cudaSetDevice(p->device);
   const int type = p->opt.precision == FIEDLER_FP64 ? 0 : 1;
-  const int nctx = std::max(1, std::min(4, p->opt.max_inflight));
+  const size_t tsz = type == 0 ? 8 : 4;
   const size_t budget = p->opt.hbm_budget_bytes ? p->opt.hbm_budget_bytes : (size_t)16 << 30;
-  const int max_batch = std::max(1, p->opt.max_batch);
+  const int max_batch = std::max(1, std::min(p->opt.max_batch, p->stage_n));
+  volatile fz::ServeDone *vd = p->done;
+  std::vector<Ticket *> adm;
   for (;;) {
     bool progressed = false;
-    // finished launches
-    for (int k = 0; k < nctx; k++) {
-      BatchCtx &c = p->bserve[k];
-      if (c.busy && cudaEventQuery(c.done) == cudaSuccess) {
-        complete_ctx(p, c);
-        progressed = true;
+    // 1. finished tickets (any order): copy their states back, complete them
+    std::vector<Ticket *> fin;
+    for (auto it = p->live.begin(); it != p->live.end();) {
+      Ticket *t = *it;
+      if (vd->done[t->k % fz::kRing] == t->k + 1ull) {
+        fin.push_back(t);
+        it = p->live.erase(it);
+      } else {
+        ++it;
       }
     }
-    // admit a new launch
-    BatchCtx *free_ctx = nullptr;
-    for (int k = 0; k < nctx && !free_ctx; k++)
-      if (!p->bserve[k].busy) free_ctx = &p->bserve[k];
+    if (!fin.empty()) {
+      progressed = true;
+      const size_t nf = std::min(fin.size(), (size_t)p->stage_n);
+      for (size_t i = 0; i < fin.size(); i += nf) {
+        const size_t m = std::min(nf, fin.size() - i);
+        bool ok = true;
+        for (size_t j = 0; j < m; j++)
+          ok = ok && cudaMemcpyAsync(p->h_stage + j, fin[i + j]->dwork, sizeof(State), cudaMemcpyDeviceToHost,
+                                     p->io_stream) == cudaSuccess;
+        ok = ok && cudaStreamSynchronize(p->io_stream) == cudaSuccess;
+        const auto now = std::chrono::steady_clock::now();
+        std::lock_guard<std::mutex> lk(p->q_mu);
+        for (size_t j = 0; j < m; j++) {
+          Ticket *t = fin[i + j];
+          const State *h = p->h_stage + j;
+          cudaFreeAsync(t->dwork, p->io_stream);
+          t->dwork = nullptr;
+          p->inflight_bytes -= t->footprint;
+          if (ok && (h->status == fz::ST_ARENA || h->status == fz::ST_SCRATCH) && t->scale < 8.0) {
+            t->scale *= 2.0;  // the hierarchy outgrew its estimate: run it again with more room
+            t->running = false;
+            p->queue.push_front(t->id);
+            continue;
+          }
+          if (ok) ticket_result(h, t);
+          else t->st = FIEDLER_ECUDA;
+          if (ok)
+            for (int ph = 0; ph < fz::PH_COUNT; ph++) p->block_seconds += h->phase_ns[1][ph] * 1e-9;
+          if (ok && (h->status == fz::ST_ARENA || h->status == fz::ST_SCRATCH)) t->st = FIEDLER_ENOMEM;
+          t->done = true;
+          t->running = false;
+          p->n_completed++;
+          p->latencies_ms.push_back(std::chrono::duration<float, std::milli>(now - t->t_submit).count());
+        }
+        p->q_cv.notify_all();
+      }
+    }
+    // 2. admissions
+    adm.clear();
     {
       std::unique_lock<std::mutex> lk(p->q_mu);
-      if (p->stop) return;
-      if (free_ctx && !p->queue.empty()) {
-        BatchCtx &c = *free_ctx;
-        c.items.clear();
-        c.type = type;
-        bool any_inflight = p->inflight_bytes > 0;
-        while (!p->queue.empty() && (int)c.items.size() < max_batch) {
-          auto itk = p->tickets.find(p->queue.front());
-          if (itk == p->tickets.end()) {
-            p->queue.pop_front();
-            continue;
-          }
-          Ticket *t = itk->second;
-          if (t->canceled) {
-            p->queue.pop_front();
-            t->st = FIEDLER_ECANCELED;
-            t->done = true;
-            p->q_cv.notify_all();
-            continue;
-          }
-          const bool fits = p->inflight_bytes + t->footprint <= budget;
-          if (!fits && (any_inflight || !c.items.empty())) break;  // wait for memory to free up
+      if (p->stop) break;
+      while (!p->queue.empty() && (int)adm.size() < max_batch && p->live.size() + adm.size() < fz::kRing - 1) {
+        auto itk = p->tickets.find(p->queue.front());
+        if (itk == p->tickets.end()) {
           p->queue.pop_front();
-          t->running = true;
-          p->inflight_bytes += t->footprint;
-          p->peak_inflight = std::max(p->peak_inflight, p->inflight_bytes);
-          BatchItem it{};
-          it.n = t->n;
-          it.nnz = t->nnz;
-          it.rp = t->rowptr;
-          it.ci = t->col;
-          it.w = t->w;
-          it.wf64 = t->w_dtype == FIEDLER_W_F64;
-          it.host_in = false;
-          it.user_x = t->x;
-          it.user_x_dev = 1;
-          it.ticket = t;
-          c.items.push_back(it);
-        }
-        if (!c.items.empty()) {
-          p->n_batches++;
-          p->n_batched_tickets += c.items.size();
-          c.busy = true;
-          lk.unlock();
-          if (batch_launch(p, c, 1.0) != FIEDLER_OK) {
-            std::lock_guard<std::mutex> lk2(p->q_mu);
-            for (auto &it : c.items) {
-              it.ticket->st = FIEDLER_ECUDA;
-              it.ticket->done = true;
-              it.ticket->running = false;
-              p->inflight_bytes -= it.ticket->footprint;
-            }
-            c.items.clear();
-            c.busy = false;
-            p->q_cv.notify_all();
-          }
-          progressed = true;
           continue;
         }
-      }
-      bool any_busy = false;
-      for (int k = 0; k < nctx; k++) any_busy |= p->bserve[k].busy;
-      if (!progressed) {
-        if (any_busy) p->q_cv.wait_for(lk, std::chrono::microseconds(50));
-        else p->q_cv.wait(lk, [&] { return p->stop || !p->queue.empty(); });
+        Ticket *t = itk->second;
+        if (t->canceled) {
+          p->queue.pop_front();
+          t->st = FIEDLER_ECANCELED;
+          t->done = true;
+          p->q_cv.notify_all();
+          continue;
+        }
+        const bool empty = p->inflight_bytes == 0 && adm.empty();
+        if (!empty && p->inflight_bytes + t->footprint > budget) break;  // wait for memory to free up
+        p->queue.pop_front();
+        t->running = true;
+        p->inflight_bytes += t->footprint;
+        p->peak_inflight = std::max(p->peak_inflight, p->inflight_bytes);
+        adm.push_back(t);
       }
     }
+    if (!adm.empty()) {
+      progressed = true;
+      int staged = 0;
+      std::vector<Ticket *> ok_t;
+      for (Ticket *t : adm) {
+        const size_t ab = r256((size_t)(arena_estimate(t->n, t->nnz, tsz, t->w_dtype == FIEDLER_W_F64) * t->scale));
+        const size_t sb = r256((size_t)(scratch_estimate(t->n, t->nnz, 1) * t->scale));
+        const size_t bytes = r256(sizeof(State)) + ab + sb;
+        if (cudaMallocFromPoolAsync((void **)&t->dwork, bytes, p->pool, p->io_stream) != cudaSuccess) {
+          t->dwork = nullptr;
+          std::lock_guard<std::mutex> lk(p->q_mu);
+          p->inflight_bytes -= t->footprint;
+          t->st = FIEDLER_ENOMEM;
+          t->done = true;
+          t->running = false;
+          p->q_cv.notify_all();
+          continue;
+        }
+        State *h = p->h_stage + staged++;
+        fill_ticket_state(p, t, h, type, ab, sb);
+        cudaMemcpyAsync(t->dwork, h, sizeof(State), cudaMemcpyHostToDevice, p->io_stream);
+        ok_t.push_back(t);
+      }
+      // item pointers, then the new tail, in stream order after the states
+      const unsigned long long first = p->published;
+      const size_t m = ok_t.size();
+      for (size_t j = 0; j < m; j++) {
+        Ticket *t = ok_t[j];
+        t->k = first + j;
+        p->h_pub[j] = (unsigned long long)(uintptr_t)t->dwork;
+        p->live.push_back(t);
+      }
+      p->published = first + m;
+      p->h_pub[m] = p->published;
+      if (m > 0) {
+        const size_t pos = first % fz::kRing, part = std::min(m, (size_t)fz::kRing - pos);
+        cudaMemcpyAsync(p->d_ring->item + pos, p->h_pub, 8 * part, cudaMemcpyHostToDevice, p->io_stream);
+        if (part < m)
+          cudaMemcpyAsync(p->d_ring->item, p->h_pub + part, 8 * (m - part), cudaMemcpyHostToDevice, p->io_stream);
+        cudaMemcpyAsync(&p->d_ring->tail, p->h_pub + m, 8, cudaMemcpyHostToDevice, p->io_stream);
+      }
+      cudaStreamSynchronize(p->io_stream);
+      std::lock_guard<std::mutex> lk(p->q_mu);
+      p->n_batches++;
+      p->n_batched_tickets += ok_t.size();
+
+    }
+    // 3. blocks for the published work: every unfinished ticket needs one;
+    // blocks that find nothing to do leave after a short wait, so the alive
+    // count is read from their exit flags and topped up with a new launch
+    // (up to the blocks that fit on the device) when it falls short
+    if (!p->live.empty()) {
+      int alive = 0, freei = -1;
+      unsigned long long oldest = p->block_next;
+      for (int i = 0; i < (int)p->serve.size(); i++) {
+        fiedler_plan::ServeLaunch &L = p->serve[i];
+        if (L.running && cudaEventQuery(L.ev) == cudaSuccess) L.running = false;
+        if (!L.running) {
+          if (freei < 0) freei = i;
+          continue;
+        }
+        int gone = 0;
+        for (int b = 0; b < L.nb; b++) {
+          const unsigned long long g = L.base + (unsigned long long)b;
+          gone += vd->exited[g % fz::kExitRing] == g + 1ull;
+        }
+        alive += L.nb - gone;
+        oldest = std::min(oldest, L.base);
+      }
+      int unfinished = 0;
+      for (Ticket *t : p->live) unfinished += vd->done[t->k % fz::kRing] != t->k + 1ull;
+      const int var = p->batch_var;
+      const int room = p->serve_slots[type][var] - alive;
+      p->live_sum += (double)unfinished;
+      p->alive_sum += (double)alive;
+      p->live_rounds++;
+      const int want = std::min(unfinished - alive, room);
+      // block numbers stay within the exit-flag ring of every running launch
+      const bool fits = p->block_next + fz::kServeSlots - oldest < (unsigned long long)fz::kExitRing;
+      if (want > 0 && fits && (freei >= 0 || p->serve.size() < 4096)) {
+        if (freei < 0) {
+          fiedler_plan::ServeLaunch L;
+          if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) == cudaSuccess) {
+            p->serve.push_back(L);
+            freei = (int)p->serve.size() - 1;
+          } else {
+            if (L.stream) cudaStreamDestroy(L.stream);
+          }
+        }
+        if (freei >= 0) {
+          // fill the device: blocks with nothing to do leave after kIdleNs
+          fiedler_plan::ServeLaunch &L = p->serve[freei];
+          const int nb = std::min(room, fz::kServeSlots);
+          unsigned long long base = p->block_next;
+          void *args[] = {(void *)&p->d_ring, (void *)&p->done_dev, (void *)&base};
+          if (cudaLaunchKernel(p->ks[type].serve_v[var], dim3(nb), dim3(fz::kBatchThreads[var]), args, 0, L.stream) ==
+                  cudaSuccess &&
+              cudaEventRecord(L.ev, L.stream) == cudaSuccess) {
+            L.running = true;
+            L.base = base;
+            L.nb = nb;
+            p->block_next += (unsigned long long)nb;
+            p->n_launches++;
+          }
+        }
+      }
+    }
+    if (!progressed) {
+      std::unique_lock<std::mutex> lk(p->q_mu);
+      if (p->stop) break;
+      if (p->live.empty() && p->queue.empty()) p->q_cv.wait(lk, [&] { return p->stop || !p->queue.empty(); });
+      else p->q_cv.wait_for(lk, std::chrono::microseconds(50));
+    }
   }
+  // leaving: let the kernel's blocks go, wait for them, release what is in flight
+  {
+    const unsigned long long one = 1;
+    cudaMemcpyAsync(&p->d_ring->stop, &one, 8, cudaMemcpyHostToDevice, p->io_stream);
+    cudaStreamSynchronize(p->io_stream);
+  }
+  for (auto &L : p->serve) {
+    if (L.running) cudaEventSynchronize(L.ev);
+    L.running = false;
+  }
+  for (Ticket *t : p->live) {
+    if (t->dwork) cudaFreeAsync(t->dwork, p->io_stream);
+    t->dwork = nullptr;
+  }
+  p->live.clear();
 }
 
 }  // namespace
@@ -763,7 +945,8 @@ void fiedler_options_default(fiedler_options *o) {
   o->fault_inject = 0;
   o->hbm_budget_bytes = 0;
   o->max_batch = 1024;
-  o->max_inflight = 2;
+  o->queue_budget_bytes = 0;
+  o->batch_threads = 0;
 }
 
 fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_stream, fiedler_plan **out) {
@@ -776,7 +959,8 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
       o.max_levels < 1 || o.max_levels > fz::kMaxLevels || !(o.stall_ratio > 0.0 && o.stall_ratio <= 1.0) ||
       o.gs_sweeps < 0 || o.pi_max_iters < 0 || o.pi_max_iters_coarsest < 0 || !(o.pi_cos_tol >= 0.0) ||
       !(o.resid_tol >= 0.0) || (o.tie_rule != 0 && o.tie_rule != 1) || o.tail_max_n < 1 || o.tail_max_nnz < 1 ||
-      o.barrier_timeout_ms < 1 || o.max_batch < 1 || o.max_inflight < 1 || o.max_inflight > 4)
+      o.barrier_timeout_ms < 1 || o.max_batch < 1 ||
+      (o.batch_threads != 0 && o.batch_threads != 512 && o.batch_threads != 256 && o.batch_threads != 128))
     return FIEDLER_EINVAL;
   fiedler_plan *p = new (std::nothrow) fiedler_plan();
   if (!p) return FIEDLER_ENOMEM;
@@ -807,20 +991,47 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
       p->grid_blocks[t][k] = g > fz::kMaxBlocks ? fz::kMaxBlocks : g;
     }
   }
-  for (int t = 0; t < 2; t++) {
-    int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->ks[t].batch, fz::kCtaThreads, 0) != cudaSuccess ||
-        bps < 1)
-      return fail(FIEDLER_ECUDA);
-    p->batch_slots[t] = bps * p->sms;
-  }
+  for (int t = 0; t < 2; t++)
+    for (int v = 0; v < 3; v++) {
+      int bps = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->ks[t].batch_v[v], fz::kBatchThreads[v], 0) !=
+              cudaSuccess ||
+          bps < 1)
+        return fail(FIEDLER_ECUDA);
+      p->batch_slots[t][v] = bps * p->sms;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p->ks[t].serve_v[v], fz::kBatchThreads[v], 0) !=
+              cudaSuccess ||
+          bps < 1)
+        return fail(FIEDLER_ECUDA);
+      p->serve_slots[t][v] = bps * p->sms;
+    }
+  p->batch_var = o.batch_threads == 256 ? 1 : o.batch_threads == 128 ? 2 : 0;
   p->bsync.stream = p->stream;
   if (cudaEventCreateWithFlags(&p->bsync.done, cudaEventDisableTiming) != cudaSuccess) return fail(FIEDLER_ECUDA);
-  for (int k = 0; k < 4; k++) {
-    BatchCtx &c = p->bserve[k];
-    if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FIEDLER_ECUDA);
-    c.own_stream = true;
-    if (cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) return fail(FIEDLER_ECUDA);
+  if (cudaHostAlloc((void **)&p->done, sizeof(fz::ServeDone), cudaHostAllocMapped) != cudaSuccess)
+    return fail(FIEDLER_ENOMEM);
+  memset(p->done, 0, sizeof(fz::ServeDone));
+  if (cudaHostGetDevicePointer((void **)&p->done_dev, p->done, 0) != cudaSuccess) return fail(FIEDLER_ECUDA);
+  if (cudaMalloc(&p->d_ring, sizeof(fz::ServeRing)) != cudaSuccess) return fail(FIEDLER_ENOMEM);
+  if (cudaMemset(p->d_ring, 0, sizeof(fz::ServeRing)) != cudaSuccess) return fail(FIEDLER_ECUDA);
+  {
+    const unsigned long long idle = fiedler_plan::kIdleNs;
+    if (cudaMemcpy(&p->d_ring->idle_ns, &idle, 8, cudaMemcpyHostToDevice) != cudaSuccess) return fail(FIEDLER_ECUDA);
+  }
+  p->stage_n = std::max(1, std::min(o.max_batch, 256));
+  if (cudaMallocHost((void **)&p->h_pub, 8 * (size_t)(p->stage_n + 1)) != cudaSuccess) return fail(FIEDLER_ENOMEM);
+  if (cudaMallocHost((void **)&p->h_stage, sizeof(State) * (size_t)p->stage_n) != cudaSuccess)
+    return fail(FIEDLER_ENOMEM);
+  if (cudaStreamCreateWithFlags(&p->io_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FIEDLER_ECUDA);
+  {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = p->device;
+    if (cudaMemPoolCreate(&p->pool, &props) != cudaSuccess) return fail(FIEDLER_ECUDA);
+    uint64_t keep = UINT64_MAX;  // freed blocks stay in the pool for the next tickets
+    if (cudaMemPoolSetAttribute(p->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
+      return fail(FIEDLER_ECUDA);
   }
   if (cudaMalloc(&p->d_state, sizeof(State)) != cudaSuccess) return fail(FIEDLER_ENOMEM);
   if (cudaMalloc(&p->d_ipart, sizeof(fz::IRed) * 2 * fz::kMaxBlocks) != cudaSuccess) return fail(FIEDLER_ENOMEM);
@@ -854,16 +1065,36 @@ fiedler_status fiedler_batch_submit(fiedler_plan *p, const fiedler_graph *g, uin
   t->w_dtype = g->w_dtype;
   const size_t wsz = g->w_dtype == FIEDLER_W_F64 ? 8 : 4;
   const size_t m = (size_t)(g->nnz > 0 ? g->nnz : 1);
-  cudaError_t e = cudaMalloc(&t->rowptr, 4 * (size_t)(g->n + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&t->col, 4 * m);
-  if (e == cudaSuccess) e = cudaMalloc(&t->w, wsz * m);
-  if (e == cudaSuccess) e = cudaMalloc(&t->x, 8 * (size_t)g->n);
+  const size_t rb = r256(4 * (size_t)(g->n + 1)), cb = r256(4 * m), wb = r256(wsz * m);
+  t->bytes = rb + cb + wb + 8 * (size_t)g->n;
+  {
+    // back-pressure: one ticket always fits into an empty queue
+    const size_t qb = p->opt.queue_budget_bytes ? p->opt.queue_budget_bytes : (size_t)8 << 30;
+    std::lock_guard<std::mutex> lk(p->q_mu);
+    if (p->queued_bytes > 0 && p->queued_bytes + t->bytes > qb) {
+      delete t;
+      return FIEDLER_EAGAIN;
+    }
+    p->queued_bytes += t->bytes;
+  }
+  cudaError_t e = cudaMallocFromPoolAsync((void **)&t->buf, t->bytes, p->pool, p->io_stream);
+  if (e == cudaSuccess) {
+    t->rowptr = (int32_t *)t->buf;
+    t->col = (int32_t *)(t->buf + rb);
+    t->w = t->buf + rb + cb;
+    t->x = (double *)(t->buf + rb + cb + wb);
+  } else {
+    t->buf = nullptr;
+  }
   const cudaMemcpyKind kind = g->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (e == cudaSuccess) e = cudaMemcpy(t->rowptr, g->rowptr, 4 * (size_t)(g->n + 1), kind);
-  if (e == cudaSuccess && g->nnz > 0) e = cudaMemcpy(t->col, g->col, 4 * (size_t)g->nnz, kind);
-  if (e == cudaSuccess && g->nnz > 0) e = cudaMemcpy(t->w, g->w, wsz * (size_t)g->nnz, kind);
+  cudaStream_t io = p->io_stream;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t->rowptr, g->rowptr, 4 * (size_t)(g->n + 1), kind, io);
+  if (e == cudaSuccess && g->nnz > 0) e = cudaMemcpyAsync(t->col, g->col, 4 * (size_t)g->nnz, kind, io);
+  if (e == cudaSuccess && g->nnz > 0) e = cudaMemcpyAsync(t->w, g->w, wsz * (size_t)g->nnz, kind, io);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(io);  // the copies only: the input may be freed on return
   if (e != cudaSuccess) {
-    free_ticket(t);
+    std::lock_guard<std::mutex> lk(p->q_mu);
+    free_ticket(p, t);
     return map_cuda(e);
   }
   t->footprint = item_footprint(g->n, g->nnz, p->opt.precision == FIEDLER_FP64 ? 8 : 4, g->w_dtype == FIEDLER_W_F64);
@@ -911,6 +1142,51 @@ fiedler_status fiedler_solve_batch(fiedler_plan *p, const fiedler_graph *graphs,
   return batch_run_sync(p, c);
 }
 
+fiedler_status fiedler_plan_autotune(fiedler_plan *p, const fiedler_graph *graphs, int count, fiedler_tuning *out) {
+  if (!p || !graphs || count < 1 || p->opt.batch_threads != 0) return FIEDLER_EINVAL;
+  std::lock_guard<std::mutex> ex(p->exec_mu);
+  std::vector<fiedler_result> res((size_t)count);
+  BatchCtx &c = p->bsync;
+  auto run = [&](int var, float *ms) -> fiedler_status {
+    p->batch_var = var;
+    c.items.clear();
+    c.type = p->opt.precision == FIEDLER_FP64 ? 0 : 1;
+    for (int i = 0; i < count; i++) {
+      const fiedler_graph &g = graphs[i];
+      fiedler_status st = check_graph(&g, &res[i]);
+      if (st != FIEDLER_OK) return st;
+      BatchItem it{};
+      it.n = g.n;
+      it.nnz = g.nnz;
+      it.rp = g.rowptr;
+      it.ci = g.col;
+      it.w = g.w;
+      it.wf64 = g.w_dtype == FIEDLER_W_F64;
+      it.host_in = !g.on_device;
+      it.user_x = nullptr;
+      it.res = &res[i];
+      c.items.push_back(it);
+    }
+    CK(cudaEventRecord(p->ev[0], p->stream));
+    fiedler_status st = batch_run_sync(p, c);
+    CK(cudaEventRecord(p->ev[1], p->stream));
+    CK(cudaEventSynchronize(p->ev[1]));
+    if (ms) CK(cudaEventElapsedTime(ms, p->ev[0], p->ev[1]));
+    return st;
+  };
+  fiedler_tuning t{};
+  fiedler_status st = run(0, nullptr);  // sizes the buffers once
+  int best = 0;
+  for (int v = 0; v < 3 && st == FIEDLER_OK; v++) {
+    st = run(v, &t.batch_ms[v]);
+    if (st == FIEDLER_OK && t.batch_ms[v] < t.batch_ms[best]) best = v;
+  }
+  p->batch_var = st == FIEDLER_OK ? best : 0;
+  t.batch_threads = fz::kBatchThreads[p->batch_var];
+  if (out) *out = t;
+  return st;
+}
+
 fiedler_status fiedler_plan_serving_stats(const fiedler_plan *cp, fiedler_serving_stats *out) {
   if (!cp || !out) return FIEDLER_EINVAL;
   fiedler_plan *p = const_cast<fiedler_plan *>(cp);
@@ -920,6 +1196,10 @@ fiedler_status fiedler_plan_serving_stats(const fiedler_plan *cp, fiedler_servin
   out->completed = p->n_completed;
   out->batches = p->n_batches;
   out->mean_batch = p->n_batches ? (double)p->n_batched_tickets / (double)p->n_batches : 0.0;
+  out->launches = p->n_launches;
+  out->block_seconds = p->block_seconds;
+  out->mean_inflight = p->live_rounds ? p->live_sum / (double)p->live_rounds : 0.0;
+  out->mean_blocks = p->live_rounds ? p->alive_sum / (double)p->live_rounds : 0.0;
   out->peak_inflight_bytes = p->peak_inflight;
   if (!p->latencies_ms.empty()) {
     std::vector<float> v = p->latencies_ms;
@@ -955,12 +1235,14 @@ fiedler_status fiedler_poll(fiedler_plan *p, uint64_t ticket, int timeout_ms, fi
     res->x_on_device = xod;
     res->status = st;
     if (x && (st == FIEDLER_OK || st == FIEDLER_ENOTCONVERGED)) {
-      cudaError_t e = cudaMemcpy(x, t->x, 8 * (size_t)t->n, xod ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+      cudaError_t e = cudaMemcpyAsync(x, t->x, 8 * (size_t)t->n,
+                                      xod ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->io_stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(p->io_stream);
       if (e != cudaSuccess) st = map_cuda(e);
     }
   }
   p->tickets.erase(it);
-  free_ticket(t);
+  free_ticket(p, t);
   return st;
 }
 
@@ -982,11 +1264,10 @@ void fiedler_plan_destroy(fiedler_plan *p) {
     p->q_cv.notify_all();
   }
   if (p->worker.joinable()) p->worker.join();
-  for (int k = 0; k < 4; k++)
-    if (p->bserve[k].stream) cudaStreamSynchronize(p->bserve[k].stream);
-  for (auto &kv : p->tickets) free_ticket(kv.second);
+  for (auto &kv : p->tickets) free_ticket(p, kv.second);
   p->tickets.clear();
-  BatchCtx *ctxs[5] = {&p->bsync, &p->bserve[0], &p->bserve[1], &p->bserve[2], &p->bserve[3]};
+  if (p->io_stream) cudaStreamSynchronize(p->io_stream);
+  std::vector<BatchCtx *> ctxs{&p->bsync};
   for (BatchCtx *c : ctxs) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->d_buf) cudaFree(c->d_buf);
@@ -1008,13 +1289,23 @@ void fiedler_plan_destroy(fiedler_plan *p) {
   for (int i = 0; i < 10; i++)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  for (auto &L : p->serve) {
+    if (L.stream) cudaStreamDestroy(L.stream);
+    if (L.ev) cudaEventDestroy(L.ev);
+  }
+  if (p->done) cudaFreeHost(p->done);
+  if (p->d_ring) cudaFree(p->d_ring);
+  if (p->h_pub) cudaFreeHost(p->h_pub);
+  if (p->h_stage) cudaFreeHost(p->h_stage);
+  if (p->io_stream) cudaStreamDestroy(p->io_stream);
+  if (p->pool) cudaMemPoolDestroy(p->pool);
   delete p;
 }
 
 const char *fiedler_status_str(fiedler_status s) {
   switch (s) {
     case FIEDLER_OK: return "ok";
-    case FIEDLER_EAGAIN: return "still in flight";
+    case FIEDLER_EAGAIN: return "still in flight (poll) or queue full (submit)";
     case FIEDLER_EINVAL: return "invalid argument or malformed graph";
     case FIEDLER_ENOMEM: return "out of device memory";
     case FIEDLER_EDISCONNECTED: return "graph is not connected";

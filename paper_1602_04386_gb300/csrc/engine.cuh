@@ -104,6 +104,7 @@ FZD void best_set(Best &b, uint64_t wk, int u, int v) {
 constexpr int kShSort = 2048;  // u64 words of the raw buffer (16 KB)
 constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one thread
 constexpr int kHeavyDeg = 32;  // rows of at least this degree are processed by a whole warp
+constexpr int kWarpNnz = 2048;  // tiny levels up to this many entries are smoothed by one warp
 
 FZD uint64_t *sh_raw() {
   __shared__ uint64_t raw[kShSort];
@@ -120,6 +121,14 @@ FZD int *sh_ints() {
 FZD long long *sh_ll() {
   __shared__ long long v[3 * 33];
   return v;
+}
+// heavy vertices (degree >= kHeavyDeg) met by a block in one colouring round
+// or matching phase, deferred to the block's warps; [kHQ] entries, then the
+// count (zero between uses).  0: colouring, 1: matching.
+constexpr int kHQ = 256;
+FZD int *sh_hq(int which) {
+  __shared__ int q[2][kHQ + 1];
+  return q[which];
 }
 FZD double *sh_bc() {  // scalars computed by one thread, read by the block
   __shared__ double v[8];
@@ -781,6 +790,7 @@ struct Eng {
       s_cnt[1] = 0;
       s_cnt[2] = 0;
       s_cnt[3] = -1;
+      sh_hq(0)[kHQ] = 0;
     }
     if (lead()) {
       S->jp_cnt[1] = 0;
@@ -819,11 +829,19 @@ struct Eng {
     int *lcur = jp.list[cur], *lnxt = jp.list[nxt];
     // threads in reverse order, so that on small levels the colouring runs on
     // other warps than the step it accompanies
+    int *hq = sh_hq(0);
     for (int q = blockDim.x - 1 - threadIdx.x; q < cnt; q += blockDim.x) {
       const int v = r == 0 ? lo + q : lcur[lo + q];
+      const int e0 = rp[v], e1 = rp[v + 1];
+      if (e1 - e0 >= kHeavyDeg) {  // to the warps, if the queue has room
+        const int k = atomicAdd(&hq[kHQ], 1);
+        if (k < kHQ) {
+          hq[k] = v;
+          continue;
+        }
+      }
       const uint64_t hv = vtx_hash(v);
       bool top = true;
-      const int e0 = rp[v], e1 = rp[v + 1];
       for (int e = e0; e < e1; e++) {
         const int u = ci[e];
         if (cround[u] >= r) {
@@ -859,11 +877,68 @@ struct Eng {
       atomicMax(&s_cnt[3], c);
     }
     __syncthreads();
+    {
+      const int nh = min(hq[kHQ], kHQ);
+      for (int k = threadIdx.x >> 5; k < nh; k += blockDim.x >> 5)
+        jp_heavy(hq[k], r, rp, ci, cround, color, lnxt + lo, &s_cnt[nxt], &s_cnt[3]);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       if (s_cnt[nxt]) atomicAdd(&S->jp_cnt[nxt], s_cnt[nxt]);
       if (s_cnt[3] >= 0) atomicMax(&S->col_max, s_cnt[3]);
       s_cnt[cur] = 0;  // becomes the append target of round r + 2
+      hq[kHQ] = 0;
       jp.visits += cnt;
+    }
+  }
+
+  // One heavy vertex's colouring round, by a whole warp: the same decision as
+  // the one-thread path (top priority among the neighbours uncoloured at the
+  // start of round r; smallest colour unused by neighbours coloured earlier),
+  // with the neighbour scans split across the lanes.
+  FZD static void jp_heavy(int v, int r, const int *rp, const int *ci, int *cround, int *color, int *lnxt,
+                           int *cnt_nxt, int *cmax) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t hv = vtx_hash(v);
+    const int e0 = rp[v], e1 = rp[v + 1];
+    for (int b = e0; b < e1; b += 32) {
+      const int e = b + lane;
+      bool beat = false;
+      if (e < e1) {
+        const int u = ci[e];
+        if (cround[u] >= r) {
+          const uint64_t hu = vtx_hash(u);
+          beat = hu > hv || (hu == hv && u > v);
+        }
+      }
+      if (__any_sync(0xffffffffu, beat)) {
+        if (lane == 0) lnxt[atomicAdd(cnt_nxt, 1)] = v;
+        return;
+      }
+    }
+    int base = 0, c = 0;
+    for (;;) {
+      uint64_t m = 0;
+      for (int e = e0 + lane; e < e1; e += 32) {
+        const int u = ci[e];
+        if (cround[u] < r) {
+          const int cu = color[u] - base;
+          if (cu >= 0 && cu < 64) m |= 1ull << cu;
+        }
+      }
+      const unsigned mlo = __reduce_or_sync(0xffffffffu, (unsigned)m);
+      const unsigned mhi = __reduce_or_sync(0xffffffffu, (unsigned)(m >> 32));
+      m = ((uint64_t)mhi << 32) | mlo;
+      if (m != ~0ull) {
+        c = base + __ffsll((long long)~m) - 1;
+        break;
+      }
+      base += 64;
+    }
+    if (lane == 0) {
+      color[v] = c;
+      cround[v] = r;
+      atomicMax(cmax, c);
     }
   }
 
@@ -899,16 +974,19 @@ struct Eng {
   }
 
   // ---- colour-order copy of the level for the solve phase -------------------
-  // Solve order: colour classes in ascending order; within a class the light
-  // rows (degree < kHeavyDeg) first, then the heavy rows, each group in
-  // ascending vertex order.  Bucket b = 2 * colour + heavy; colstart[b] is the
-  // first solve position of bucket b (2C + 1 entries).
+  // Solve order: every light row (degree < kHeavyDeg) before every heavy
+  // row; within each group colour classes in ascending order, each in
+  // ascending vertex order.  Bucket b = heavy * C + colour (C colours);
+  // colstart[b] is the first solve position of bucket b (2C + 1 entries):
+  // light rows of colour c at [colstart[c], colstart[c + 1]), heavy rows of
+  // colour c at [colstart[C + c], colstart[C + c + 1]).
   FZD bool reorder(int l) {
     cur_level = l;
     Level *L = &S->lv[l];
     const int n = L->n, nnz = L->nnz, C = 2 * L->ncolors;
     const int *rp = L->rowptr, *ci = L->col, *color = L->color;
-    auto bucket = [&](int v) { return 2 * color[v] + (rp[v + 1] - rp[v] >= kHeavyDeg ? 1 : 0); };
+    const int C0 = L->ncolors;
+    auto bucket = [&](int v) { return (rp[v + 1] - rp[v] >= kHeavyDeg ? C0 : 0) + color[v]; };
     int *hist = (int *)salloc(4ull * C * nb);
     int *perm = (int *)aalloc(4ull * n);
     int *iperm = (int *)aalloc(4ull * n);
@@ -1077,10 +1155,12 @@ struct Eng {
     int lo, hi;
     chunk(n, lo, hi);
     int *s_cnt = sh_ints();
+    int *hq = sh_hq(1);
     if (threadIdx.x == 0) {
       s_cnt[0] = hi - lo;
       s_cnt[1] = 0;
       s_cnt[2] = 0;
+      hq[kHQ] = 0;
     }
     if (lead()) {
       S->wl_cnt[1] = 0;
@@ -1097,6 +1177,13 @@ struct Eng {
       if ((ph & 1) == 0) {  // pick
         for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
           const int v = ph == 0 ? lo + q : list[cur][lo + q];
+          if (rp[v + 1] - rp[v] >= kHeavyDeg) {  // to the warps, if the queue has room
+            const int k = atomicAdd(&hq[kHQ], 1);
+            if (k < kHQ) {
+              hq[k] = v;
+              continue;
+            }
+          }
           Best b;
           best_init(b);
           for (int e = rp[v]; e < rp[v + 1]; e++) {
@@ -1106,6 +1193,33 @@ struct Eng {
             if (best_beats(b, wk, v, u, tie)) best_set(b, wk, v, u);
           }
           if (b.v >= 0) {
+            cand[v] = b.v;
+            list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
+          }
+        }
+        __syncthreads();
+        // heavy vertices: one warp each, lanes over the neighbours, then the
+        // warp's best under the same total order (unique, so the merge order
+        // does not matter)
+        const int nh = min(hq[kHQ], kHQ);
+        const int lane = threadIdx.x & 31;
+        for (int k = threadIdx.x >> 5; k < nh; k += blockDim.x >> 5) {
+          const int v = hq[k];
+          Best b;
+          best_init(b);
+          b.wk = 0;
+          for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
+            const int u = ci[e];
+            if (ph > 0 && mate[u] >= 0) continue;
+            const uint64_t wk = wl.key(e);
+            if (best_beats(b, wk, v, u, tie)) best_set(b, wk, v, u);
+          }
+          for (int o = 16; o >= 1; o >>= 1) {
+            const uint64_t owk = __shfl_xor_sync(0xffffffffu, b.wk, o);
+            const int ov = __shfl_xor_sync(0xffffffffu, b.v, o);
+            if (ov >= 0 && best_beats(b, owk, v, ov, tie)) best_set(b, owk, v, ov);
+          }
+          if (lane == 0 && b.v >= 0) {
             cand[v] = b.v;
             list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
           }
@@ -1122,6 +1236,7 @@ struct Eng {
       if (threadIdx.x == 0) {
         if (s_cnt[nxt]) atomicAdd(&S->wl_cnt[nxt], s_cnt[nxt]);
         s_cnt[cur] = 0;
+        hq[kHQ] = 0;
       }
       visits += cnt;
       if (!sync_p()) return false;
@@ -1611,7 +1726,8 @@ struct Eng {
       }
       return smooth_v<T>(l, kmax, mu, s, gs_phase);
     }
-    if (tiny(n, nnz)) return smooth_warp<double>(l, kmax, mu, s, gs_phase);
+    // one warp for the sparse tiny levels; denser ones need the whole block
+    if (tiny(n, nnz) && nnz <= kWarpNnz) return smooth_warp<double>(l, kmax, mu, s, gs_phase);
     if (vdbl(n, nnz)) return smooth_v<double>(l, kmax, mu, s, gs_phase);
     return smooth_v<T>(l, kmax, mu, s, gs_phase);
   }
@@ -1622,6 +1738,7 @@ struct Eng {
     const int n = L->n, nnz = L->nnz, C = L->ncolors;
     const int *srp = L->srowptr, *scol = L->scol, *cst = L->colstart;
     const int lane = threadIdx.x & 31, gw = tid >> 5, nwarp = nthr >> 5;
+    const int nl = cst[C];  // light rows [0, nl), heavy rows [nl, n)
     const V *sw = (const V *)L->sw;
     V *A = (V *)L->x, *B = (V *)L->y;
     const double g = S->opt.guard;
@@ -1639,14 +1756,17 @@ struct Eng {
     for (int k = 0; k < nsweeps; k++) {
       double acc[2] = {0.0, 0.0};
       for (int c = 0; c < C; c++) {
-        const int cs = cst[2 * c], hs = cst[2 * c + 1], ce = cst[2 * c + 2];
-        for (int i = cs + tid; i < hs; i += nthr) {
+        // class c: light rows [cs, ce), heavy rows [hs, he); a neighbour j is
+        // already updated in this sweep iff its class is below c
+        const int cs = cst[c], ce = cst[c + 1], hs = cst[C + c], he = cst[C + c + 1];
+        auto done = [&](int j) { return j < cs || (j >= nl && j < hs); };
+        for (int i = cs + tid; i < ce; i += nthr) {
           V num = (V)0, dsum = (V)0;
           const int e1 = srp[i + 1];
           for (int e = srp[i]; e < e1; e++) {
             const int j = scol[e];
             const V wv = sw[e];
-            const V xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
+            const V xj = done(j) ? B[j] : (A[j] - muT) * sT;
             num += wv * xj;
             dsum += wv;
           }
@@ -1655,14 +1775,14 @@ struct Eng {
           acc[0] += (double)xi;
           acc[1] += (double)xi * (double)xi;
         }
-        for (int i = hs + gw; i < ce; i += nwarp) {  // heavy rows: one warp each
+        for (int i = hs + gw; i < he; i += nwarp) {  // heavy rows: one warp each
           V num = (V)0, dsum = (V)0;
           const int e1 = srp[i + 1];
 #pragma unroll 4
           for (int e = srp[i] + lane; e < e1; e += 32) {
             const int j = scol[e];
             const V wv = sw[e];
-            const V xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
+            const V xj = done(j) ? B[j] : (A[j] - muT) * sT;
             num += wv * xj;
             dsum += wv;
           }
@@ -1723,24 +1843,23 @@ struct Eng {
           acr[1] += xd * ld;
         }
       };
-      for (int c = 0; c < C; c++) {
-        const int cs = cst[2 * c], hs = cst[2 * c + 1], ce = cst[2 * c + 2];
-        for (int i = cs + tid; i < hs; i += nthr) {
-          const V xi = A[i];
-          V lx = (V)0;
-          const int e1 = srp[i + 1];
-          for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
-          row(i, xi, lx);
-        }
-        for (int i = hs + gw; i < ce; i += nwarp) {
-          const V xi = A[i];
-          V lx = (V)0;
-          const int e1 = srp[i + 1];
+      // rows in any order here: light rows [0, nl) one thread each, heavy
+      // rows [nl, n) one warp each
+      for (int i = tid; i < nl; i += nthr) {
+        const V xi = A[i];
+        V lx = (V)0;
+        const int e1 = srp[i + 1];
+        for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
+        row(i, xi, lx);
+      }
+      for (int i = nl + gw; i < n; i += nwarp) {
+        const V xi = A[i];
+        V lx = (V)0;
+        const int e1 = srp[i + 1];
 #pragma unroll 4
-          for (int e = srp[i] + lane; e < e1; e += 32) lx += sw[e] * (xi - A[scol[e]]);
-          lx = warp_sum(lx);
-          if (lane == 0) row(i, xi, lx);
-        }
+        for (int e = srp[i] + lane; e < e1; e += 32) lx += sw[e] * (xi - A[scol[e]]);
+        lx = warp_sum(lx);
+        if (lane == 0) row(i, xi, lx);
       }
       if (!grid_dsum<4>(acc)) return false;
       if (resid && !grid_dsum<2>(acr)) return false;
@@ -1810,15 +1929,17 @@ struct Eng {
       for (int k = 0; k < nsweeps; k++) {
         double acc[2] = {0.0, 0.0};
         const V muT = (V)mu, sT = (V)s;
+        const int nl = cst[C];
         for (int c = 0; c < C; c++) {
-          const int cs = cst[2 * c], hs = cst[2 * c + 1], ce = cst[2 * c + 2];
-          for (int i = cs + lane; i < hs; i += 32) {
+          const int cs = cst[c], ce = cst[c + 1], hs = cst[C + c], he = cst[C + c + 1];
+          auto done = [&](int j) { return j < cs || (j >= nl && j < hs); };
+          for (int i = cs + lane; i < ce; i += 32) {
             V num = (V)0, dsum = (V)0;
             const int e1 = srp[i + 1];
             for (int e = srp[i]; e < e1; e++) {
               const int j = scol[e];
               const V wv = sw[e];
-              const V xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
+              const V xj = done(j) ? B[j] : (A[j] - muT) * sT;
               num += wv * xj;
               dsum += wv;
             }
@@ -1827,14 +1948,14 @@ struct Eng {
             acc[0] += (double)xi;
             acc[1] += (double)xi * (double)xi;
           }
-          for (int i = hs; i < ce; i++) {  // heavy rows: the warp together
+          for (int i = hs; i < he; i++) {  // heavy rows: the warp together
             V num = (V)0, dsum = (V)0;
             const int e1 = srp[i + 1];
 #pragma unroll 4
-          for (int e = srp[i] + lane; e < e1; e += 32) {
+            for (int e = srp[i] + lane; e < e1; e += 32) {
               const int j = scol[e];
               const V wv = sw[e];
-              const V xj = (j < cs) ? B[j] : (A[j] - muT) * sT;
+              const V xj = done(j) ? B[j] : (A[j] - muT) * sT;
               num += wv * xj;
               dsum += wv;
             }
@@ -1893,24 +2014,22 @@ struct Eng {
             acc[5] += xd * ld;
           }
         };
-        for (int c = 0; c < C; c++) {
-          const int cs = cst[2 * c], hs = cst[2 * c + 1], ce = cst[2 * c + 2];
-          for (int i = cs + lane; i < hs; i += 32) {
-            const V xi = A[i];
-            V lx = (V)0;
-            const int e1 = srp[i + 1];
-            for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
-            row(i, xi, lx);
-          }
-          for (int i = hs; i < ce; i++) {
-            const V xi = A[i];
-            V lx = (V)0;
-            const int e1 = srp[i + 1];
+        const int nl = cst[C];  // light rows [0, nl), heavy rows [nl, n)
+        for (int i = lane; i < nl; i += 32) {
+          const V xi = A[i];
+          V lx = (V)0;
+          const int e1 = srp[i + 1];
+          for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
+          row(i, xi, lx);
+        }
+        for (int i = nl; i < n; i++) {
+          const V xi = A[i];
+          V lx = (V)0;
+          const int e1 = srp[i + 1];
 #pragma unroll 4
           for (int e = srp[i] + lane; e < e1; e += 32) lx += sw[e] * (xi - A[scol[e]]);
-            lx = warp_sum(lx);
-            if (lane == 0) row(i, xi, lx);
-          }
+          lx = warp_sum(lx);
+          if (lane == 0) row(i, xi, lx);
         }
         __syncwarp();
         warp_dsum<6>(acc);
@@ -1990,11 +2109,10 @@ struct Eng {
       acc[3] += (double)lx * (double)lx;
       big.mx = max(big.mx, (long long)__double_as_longlong(fabs(xk)));
     };
-    const int *cst = L->colstart, C = L->ncolors;
+    const int nl = L->colstart[L->ncolors];  // light rows [0, nl), heavy rows [nl, n)
     const int lane = threadIdx.x & 31, gw = tid >> 5, nwarp = nthr >> 5;
-    for (int c = 0; c < C; c++) {
-      const int cs = cst[2 * c], hs = cst[2 * c + 1], ce = cst[2 * c + 2];
-      for (int k = cs + tid; k < hs; k += nthr) {
+    {
+      for (int k = tid; k < nl; k += nthr) {
         const V xi = A[k];
         V lx = (V)0, num = (V)0;
         const int e1 = srp[k + 1];
@@ -2006,7 +2124,7 @@ struct Eng {
         }
         row(xi, lx, num);
       }
-      for (int k = hs + gw; k < ce; k += nwarp) {  // heavy rows: one warp each
+      for (int k = nl + gw; k < n; k += nwarp) {  // heavy rows: one warp each
         const V xi = A[k];
         V lx = (V)0, num = (V)0;
         const int e1 = srp[k + 1];
@@ -2159,6 +2277,56 @@ FZD void batch_entry(State *states, int count, int *next, char *scratch, unsigne
     __syncthreads();
     engine_entry<T, false>(S, 1);
     __syncthreads();
+  }
+}
+
+// Serving form: resident blocks claim published tickets one at a time (each
+// ticket's state carries its own arena and scratch) and flag each one as soon
+// as it is finished, so a long solve holds only its own block.  A block with
+// no work waits briefly (bounded by ring->idle_ns, checking the ring with
+// backoff), then leaves and says so (block base + b flags exited[]); the host
+// keeps as many blocks alive as there is work, launching more when needed.
+template <class T>
+FZD void serve_entry(ServeRing *ring, ServeDone *fin, unsigned long long base) {
+  __shared__ long long s_k;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      long long got = -1;
+      const uint64_t t0 = gtime();
+      volatile ServeRing *vr = ring;
+      for (;;) {
+        const unsigned long long tail = vr->tail;
+        const unsigned long long h = vr->head;
+        if (h < tail) {
+          if (atomicCAS(&ring->head, h, h + 1) == h) {
+            got = (long long)h;
+            break;
+          }
+          continue;
+        }
+        if (vr->stop || gtime() - t0 > vr->idle_ns) break;
+        __nanosleep(2000);
+      }
+      s_k = got;
+    }
+    __syncthreads();
+    const long long k = s_k;
+    __syncthreads();
+    if (k < 0) {
+      if (threadIdx.x == 0) {
+        const unsigned long long g = base + blockIdx.x;
+        ((volatile unsigned long long *)fin->exited)[g % kExitRing] = g + 1ull;
+      }
+      return;
+    }
+    __threadfence();
+    State *S = ((State *volatile *)ring->item)[k % kRing];
+    engine_entry<T, false>(S, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence_system();  // the state's results before the flag
+      ((volatile unsigned long long *)fin->done)[k % kRing] = (unsigned long long)k + 1ull;
+    }
   }
 }
 

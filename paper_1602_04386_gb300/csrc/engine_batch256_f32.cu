@@ -1,0 +1,24 @@
+// engine_batch256_f32.cu -- float batched and serving kernels with 256 threads per graph's block
+// (2 graph(s) resident per SM); one translation unit per variant so that
+// they compile in parallel.
+#include "engine.cuh"
+#include "kernels.h"
+
+namespace fz {
+
+__global__ void __launch_bounds__(256, 2)
+    fz_batch256_f32(State *states, int count, int *next, char *scratch, unsigned long long slot_bytes) {
+  batch_entry<float>(states, count, next, scratch, slot_bytes);
+}
+__global__ void __launch_bounds__(256, 2) fz_serve256_f32(ServeRing *ring, ServeDone *fin,
+                                                              unsigned long long base) {
+  serve_entry<float>(ring, fin, base);
+}
+
+void batch_kernel256_f32(KernelSet *k) {
+  k->batch_v[1] = (const void *)fz_batch256_f32;
+  k->serve_v[1] = (const void *)fz_serve256_f32;
+  k->batch_names[1] = "fz_batch256_f32";
+}
+
+}  // namespace fz

@@ -7,20 +7,19 @@ namespace fz {
 __global__ void __launch_bounds__(kGridThreads, 2) fz_grid_setup_f64(State *S) { engine_entry<double, true>(S, 0); }
 __global__ void __launch_bounds__(kGridThreads, 2) fz_grid_solve_f64(State *S) { engine_entry<double, true>(S, 2); }
 __global__ void __launch_bounds__(kCtaThreads, 1) fz_cta_f64(State *S) { engine_entry<double, false>(S, 1); }
-__global__ void __launch_bounds__(kCtaThreads, 1)
-    fz_batch_f64(State *states, int count, int *next, char *scratch, unsigned long long slot_bytes) {
-  batch_entry<double>(states, count, next, scratch, slot_bytes);
-}
 
 void kernels_f64(KernelSet *k) {
   k->grid_setup = (const void *)fz_grid_setup_f64;
   k->grid_solve = (const void *)fz_grid_solve_f64;
   k->cta = (const void *)fz_cta_f64;
-  k->batch = (const void *)fz_batch_f64;
   k->names[0] = "fz_grid_setup_f64";
   k->names[1] = "fz_cta_f64";
   k->names[2] = "fz_grid_solve_f64";
-  k->names[3] = "fz_batch_f64";
+  batch_kernel512_f64(k);
+  batch_kernel256_f64(k);
+  batch_kernel128_f64(k);
+  k->batch = k->batch_v[0];
+  k->names[3] = k->batch_names[0];
 }
 
 }  // namespace fz

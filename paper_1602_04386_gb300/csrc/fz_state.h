@@ -127,4 +127,27 @@ struct State {
   Level lv[kMaxLevels];
 };
 
+// Serving ring.  The host publishes ticket states item[k % kRing] for
+// k < tail (device memory, written by copies on one stream: items before the
+// tail); resident blocks of the serving kernel claim items through the
+// device counter head and, once item k is finished, write done[k % kRing] =
+// k + 1 into host-mapped memory.  The host keeps fewer than kRing items
+// unfinished.
+constexpr int kRing = 4096;
+struct ServeRing {               // device memory
+  unsigned long long tail;       // items published
+  unsigned long long head;       // items claimed
+  unsigned long long stop;       // 1: the kernel's blocks leave as soon as they are idle
+  unsigned long long idle_ns;    // a block with no work for this long leaves
+  State *item[kRing];
+};
+constexpr int kServeSlots = 1024;    // blocks of one serving launch, at most
+constexpr int kExitRing = 1 << 16;  // exit flags of the most recent serving blocks
+struct ServeDone {                   // host-mapped pinned memory
+  unsigned long long done[kRing];
+  // serving blocks are numbered across launches; block g writes
+  // exited[g % kExitRing] = g + 1 when it leaves
+  unsigned long long exited[kExitRing];
+};
+
 }  // namespace fz

@@ -44,7 +44,7 @@ SYMBOLS = (
     "fiedler_poll", "fiedler_cancel", "fiedler_plan_destroy", "fiedler_status_str",
     "fiedler_plan_num_levels", "fiedler_plan_level_info", "fiedler_plan_copy_level",
     "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc",
-    "fiedler_solve_batch", "fiedler_plan_serving_stats",
+    "fiedler_solve_batch", "fiedler_plan_serving_stats", "fiedler_plan_autotune",
 )
 
 
@@ -68,7 +68,8 @@ class fiedler_options(C.Structure):
         ("fault_inject", C.c_int),
         ("hbm_budget_bytes", C.c_size_t),
         ("max_batch", C.c_int),
-        ("max_inflight", C.c_int),
+        ("queue_budget_bytes", C.c_size_t),
+        ("batch_threads", C.c_int),
     ]
 
 
@@ -127,6 +128,17 @@ class fiedler_serving_stats(C.Structure):
         ("mean_ms", C.c_double),
         ("mean_batch", C.c_double),
         ("peak_inflight_bytes", C.c_size_t),
+        ("launches", C.c_uint64),
+        ("block_seconds", C.c_double),
+        ("mean_inflight", C.c_double),
+        ("mean_blocks", C.c_double),
+    ]
+
+
+class fiedler_tuning(C.Structure):
+    _fields_ = [
+        ("batch_threads", C.c_int),
+        ("batch_ms", C.c_float * 3),
     ]
 
 
@@ -185,10 +197,11 @@ def load():
                                             C.POINTER(fiedler_result)]
         L.fiedler_solve_batch.argtypes = [vp, C.POINTER(fiedler_graph), C.c_int, C.POINTER(fiedler_result)]
         L.fiedler_plan_serving_stats.argtypes = [vp, C.POINTER(fiedler_serving_stats)]
+        L.fiedler_plan_autotune.argtypes = [vp, C.POINTER(fiedler_graph), C.c_int, C.POINTER(fiedler_tuning)]
         for f in ("fiedler_plan_create", "fiedler_solve", "fiedler_batch_submit", "fiedler_poll", "fiedler_cancel",
                   "fiedler_plan_num_levels", "fiedler_plan_level_info", "fiedler_plan_copy_level",
                   "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc",
-                  "fiedler_solve_batch", "fiedler_plan_serving_stats"):
+                  "fiedler_solve_batch", "fiedler_plan_serving_stats", "fiedler_plan_autotune"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -262,6 +275,13 @@ def fiedler_plan_get_profile(plan):
 def fiedler_solve_batch(plan, graphs, results) -> int:
     """graphs: ctypes array of fiedler_graph; results: ctypes array of fiedler_result."""
     return load().fiedler_solve_batch(plan, graphs, len(graphs), results)
+
+
+def fiedler_plan_autotune(plan, graphs) -> tuple[int, fiedler_tuning]:
+    """graphs: ctypes array of fiedler_graph (the sample)."""
+    out = fiedler_tuning()
+    st = load().fiedler_plan_autotune(plan, graphs, len(graphs), C.byref(out))
+    return st, out
 
 
 def fiedler_plan_serving_stats(plan):
@@ -439,6 +459,20 @@ class Plan:
 
     def serving_stats(self) -> fiedler_serving_stats:
         st, out = fiedler_plan_serving_stats(self.h)
+        return out
+
+    def autotune(self, graphs, on_device=True) -> fiedler_tuning:
+        """Autotunes the batched form's block size on a sample of inputs.CSR graphs."""
+        keep = []
+        garr = (fiedler_graph * len(graphs))()
+        for i, g in enumerate(graphs):
+            gs, k = device_graph(g) if on_device else host_graph(g)
+            keep.append(k)
+            garr[i] = gs
+        st, out = fiedler_plan_autotune(self.h, garr)
+        del keep
+        if st != FIEDLER_OK:
+            raise FiedlerError(st, "fiedler_plan_autotune")
         return out
 
     def solve_batch_struct(self, garr, rarr) -> int:

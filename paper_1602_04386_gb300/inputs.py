@@ -316,3 +316,27 @@ def batch_mix(count: int = 4096, seed: int = BASE_SEED + 4, scale_range=(9, 16),
         for part in ex.map(_batch_items, jobs):
             out.extend(part)
     return out
+
+
+def _knn_item(args):
+    npts, seed = args
+    return knn_mixture(int(npts), seed=seed)
+
+
+def serving_pool(count: int = 24, nmin: float = 1e3, nmax: float = 2e6, seed: int = BASE_SEED + 5, procs: int = 1):
+    """Graphs for the serving workload: Gaussian-mixture kNN graphs (as
+    knn_mixture) with point counts log-spaced from nmin to nmax, graph i
+    drawn with seed + i.  Requests that pick one of them uniformly at random
+    have sizes distributed log-uniformly between nmin and nmax (to the pool's
+    resolution)."""
+    sizes = np.exp(np.linspace(np.log(nmin), np.log(nmax), count)).round().astype(np.int64)
+    jobs = [(int(sz), seed + i) for i, sz in enumerate(sizes)]
+    if procs <= 1:
+        return [_knn_item(j) for j in jobs]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    # largest first, so that the longest jobs start early
+    order = sorted(range(count), key=lambda i: -sizes[i])
+    with cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
+        res = dict(zip(order, ex.map(_knn_item, [jobs[i] for i in order])))
+    return [res[i] for i in range(count)]

@@ -87,7 +87,7 @@ def test_serving_tickets_alone_and_in_the_mix():
     as memory and launch slots free up) give the same result as alone."""
     gs = mixed_grids(24, seed=5)
     want = [alone(g, fiedler.FIEDLER_FP32_FP64RED) for g in gs]
-    with fiedler.Plan(max_batch=5, max_inflight=2) as p:
+    with fiedler.Plan(max_batch=5) as p:
         tickets = []
         for i, g in enumerate(gs):
             tickets.append(p.submit(g))
@@ -105,7 +105,7 @@ def test_serving_tickets_alone_and_in_the_mix():
 def test_serving_memory_budget_admits_one_at_a_time():
     gs = mixed_grids(5, seed=9)
     want = [alone(g, fiedler.FIEDLER_FP32_FP64RED) for g in gs]
-    with fiedler.Plan(hbm_budget_bytes=1, max_inflight=2) as p:
+    with fiedler.Plan(hbm_budget_bytes=1) as p:
         tickets = [p.submit(g) for g in gs]
         for g, t, a in zip(gs, tickets, want):
             st, r = p.poll(t, -1, n=g.n)
@@ -115,7 +115,7 @@ def test_serving_memory_budget_admits_one_at_a_time():
 
 
 def test_serving_cancel_and_poll_timeout():
-    with fiedler.Plan(max_inflight=1) as p:
+    with fiedler.Plan(max_batch=1) as p:
         big = inputs.grid(200, 150, "uniform", seed=2)
         ts = [p.submit(big) for _ in range(3)]
         p.cancel(ts[2])
@@ -126,3 +126,55 @@ def test_serving_cancel_and_poll_timeout():
             assert st == fiedler.FIEDLER_OK
         st, _ = p.poll(ts[2], -1)
         assert st in (fiedler.FIEDLER_ECANCELED, fiedler.FIEDLER_OK)
+
+
+def test_submit_back_pressure():
+    """With the queue budget used up, submit returns EAGAIN without queueing;
+    once the earlier ticket is polled, the same submit succeeds."""
+    g = inputs.grid(40, 30, "unit")
+    gs, keep = fiedler.host_graph(g)
+    with fiedler.Plan(queue_budget_bytes=1) as p:
+        st, t1 = fiedler.fiedler_batch_submit(p.h, gs)  # an empty queue always takes one
+        assert st == fiedler.FIEDLER_OK
+        st, _ = fiedler.fiedler_batch_submit(p.h, gs)
+        assert st == fiedler.FIEDLER_EAGAIN
+        assert fiedler.fiedler_poll(p.h, t1, -1, fiedler.fiedler_result()) == fiedler.FIEDLER_OK
+        st, t2 = fiedler.fiedler_batch_submit(p.h, gs)
+        assert st == fiedler.FIEDLER_OK
+        r = fiedler.fiedler_result()
+        assert fiedler.fiedler_poll(p.h, t2, -1, r) == fiedler.FIEDLER_OK
+        with fiedler.Plan() as q:
+            a = q.solve(g)
+        assert abs(r.lambda2 - a.lambda2) <= 1e-5 * a.lambda2
+    del keep
+
+
+@pytest.mark.parametrize("threads", [256, 128])
+def test_block_size_variants(threads):
+    """Every block size of the batched kernel: a graph's result is the same
+    alone and in a mixed batch (bit for bit), and grids agree with the
+    512-thread kernel to the FP32-form tolerance."""
+    gs = inputs.batch_mix(8, scale_range=(8, 10), side_range=(20, 60))
+    with fiedler.Plan(batch_threads=threads) as p:
+        mix = p.solve_batch(gs)
+        alone = [p.solve_batch([g])[0] for g in gs]
+    with fiedler.Plan(batch_threads=512) as q:
+        ref = q.solve_batch(gs)
+    for g, a, b, c in zip(gs, mix, alone, ref):
+        assert a.status == b.status == fiedler.FIEDLER_OK
+        assert a.lambda2 == b.lambda2 and np.array_equal(a.x, b.x)
+        if g.name.startswith("grid"):
+            assert abs(a.lambda2 - c.lambda2) <= 1e-5 * c.lambda2
+
+
+def test_autotune_picks_a_block_size():
+    gs = inputs.batch_mix(12, scale_range=(8, 10), side_range=(20, 80))
+    with fiedler.Plan() as p:
+        t = p.autotune(gs)
+        assert t.batch_threads in (512, 256, 128)
+        assert all(ms > 0 for ms in t.batch_ms)
+        res = p.solve_batch(gs)
+        assert all(r.status == fiedler.FIEDLER_OK for r in res)
+    with fiedler.Plan(batch_threads=256) as q:
+        st, _ = fiedler.fiedler_plan_autotune(q.h, (fiedler.fiedler_graph * 1)())
+        assert st == fiedler.FIEDLER_EINVAL  # a fixed block size is not tuned
