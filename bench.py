@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -99,7 +100,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(os.environ.get("FIEDLER_BENCH_LOGDIR", tempfile.gettempdir()),
+                                 f"fiedler_clocks_rank{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -248,15 +248,16 @@ fiedler_status fiedler_plan_serving_stats(const fiedler_plan *plan, fiedler_serv
 
 typedef struct {
   int batch_threads;         /* block size chosen for this plan's batched and served launches */
-  float batch_ms[3];         /* CUDA-event time of the sample batch with 512, 256 and 128
-                                threads per graph (0 = not measured) */
+  float batch_ms[3];         /* CUDA-event time of the repeated sample batch with 512, 256
+                                and 128 threads per graph (0 = not measured) */
 } fiedler_tuning;
 
 /* Autotuner of the batched form (a project addition; the paper has none):
- * solves the `count` sample graphs as one batch with each block size (512,
- * 256 and 128 threads per graph, i.e. 1, 2 and 4 graphs resident per SM),
- * keeps the fastest for every later fiedler_solve_batch and serving launch of
- * this plan, and reports the timings.  Results depend on the block size only
+ * solves the `count` sample graphs, repeated until every block size has at
+ * least two graphs per resident block, as one batch with each block size
+ * (512, 256 and 128 threads per graph, i.e. 1, 2 and 4 graphs resident per
+ * SM), keeps the fastest for every later fiedler_solve_batch and serving
+ * launch of this plan, and reports the timings of the repeated sample.  Results depend on the block size only
  * through the rounding of block-wide sums, so a graph gives the same result in
  * any batch of a tuned plan; the sample results are discarded.  Returns EINVAL
  * for an empty sample or a plan created with a fixed batch_threads. */

@@ -1145,14 +1145,19 @@ fiedler_status fiedler_solve_batch(fiedler_plan *p, const fiedler_graph *graphs,
 fiedler_status fiedler_plan_autotune(fiedler_plan *p, const fiedler_graph *graphs, int count, fiedler_tuning *out) {
   if (!p || !graphs || count < 1 || p->opt.batch_threads != 0) return FIEDLER_EINVAL;
   std::lock_guard<std::mutex> ex(p->exec_mu);
-  std::vector<fiedler_result> res((size_t)count);
+  // throughput, not the latency of the largest graph: the sample is repeated
+  // until every variant has at least two graphs per resident block
+  const int type = p->opt.precision == FIEDLER_FP64 ? 0 : 1;
+  int total = count;
+  for (int v = 0; v < 3; v++) total = std::max(total, 2 * p->batch_slots[type][v]);
+  std::vector<fiedler_result> res((size_t)total);
   BatchCtx &c = p->bsync;
   auto run = [&](int var, float *ms) -> fiedler_status {
     p->batch_var = var;
     c.items.clear();
-    c.type = p->opt.precision == FIEDLER_FP64 ? 0 : 1;
-    for (int i = 0; i < count; i++) {
-      const fiedler_graph &g = graphs[i];
+    c.type = type;
+    for (int i = 0; i < total; i++) {
+      const fiedler_graph &g = graphs[i % count];
       fiedler_status st = check_graph(&g, &res[i]);
       if (st != FIEDLER_OK) return st;
       BatchItem it{};

@@ -11,10 +11,14 @@ reference ``splitmix64.c``): output k (k = 0, 1, ...) of the stream seeded with
 is ``(output >> 11) * 2**-53``.  Every weight is rounded to float32 so that the
 FP32 and FP64 forms of the solver see the same graph.
 
-Workload shapes (the recipe is restated in the design doc):
+Workload shapes:
   * unit 2-D 5-point grids (vertex index r*k + c, r < m, c < k);
   * weighted 2-D grids, edges enumerated horizontal (row-major) then vertical,
     weight_e = f32(0.5 + u_e), u_e the e-th uniform draw of the seed's stream;
+  * R-MAT graphs (skewed degrees) and Gaussian-mixture k-nearest-neighbour
+    graphs (spectral clustering inputs), largest connected component kept;
+  * the batched mix (grids and R-MAT graphs of many sizes) and the serving
+    pool (kNN graphs of log-spaced sizes);
   * small closed-form families (path, cycle, complete, star) for pins;
   * random sparse graphs for dense-eigensolver pins.
 """

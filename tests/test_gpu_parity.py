@@ -244,3 +244,14 @@ def test_full_size_grid_fp32_sampled():
         assert p.num_levels == ref.num_levels
         assert abs(r.lambda2 - ref.lam) <= 1e-5 * ref.lam
         assert abs(np.linalg.norm(r.x) - 1) < 1e-9 and r.ortho < 1e-9
+
+
+@pytest.mark.parametrize("precision,tol", [(FP64, 1e-10), (FP32, 1e-5)])
+def test_original_cmg_variant_pi_only(precision, tol):
+    """gs_sweeps = 0 is the original cascadic multigrid that the method
+    modifies (Sec. 2: the two differ only in the Gauss-Seidel smoothing, so
+    without it every level runs power iteration alone): same kernels, same
+    parity bar against the oracle run with gs_sweeps = 0."""
+    g = inputs.grid(160, 120, "uniform", seed=11)
+    r, ref = compare(g, precision, tol, gs_sweeps=0)
+    assert r.gs_sweeps_total == 0
