@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-from paper_1602_04386_gb300 import inputs  # noqa: E402
+from paper_1602_04386_gb300 import inputs, shard  # noqa: E402
 
 METRIC = "Fiedler solves/s & SpMV/GS HBM GB/s at lambda2 rel err <=1e-5 vs plain; p50/p99 ms"
 WORKLOAD = dict(m=2048, k=1536, weights="uniform", seed=inputs.BASE_SEED + 2)
@@ -47,11 +47,7 @@ def make_graph(w=WORKLOAD):
     return inputs.grid(w["m"], w["k"], w["weights"], seed=w["seed"])
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+dist_env = shard.dist_env
 
 
 def measured_peaks():
@@ -156,7 +152,7 @@ def batch_name(count):
             f"odd: R-MAT a=.57 b=c=.19 scale U[9,16] ef 8 w U[.1,1))")
 
 
-def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15):
+def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15, dist=None):
     """The batched form on the batch workload: one fiedler_solve_batch call per
     step over all graphs (device-resident inputs and outputs), FP32 form; the
     plain single-graph FP64 form on every plain_every-th graph for solves/s and
@@ -195,9 +191,10 @@ def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15):
         return e0.elapsed_time(e1), wall
 
     plan = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP32_FP64RED)
-    # autotuner: block size per graph chosen on every 16th graph of the batch
-    tsample = (fiedler.fiedler_graph * len(range(0, count, 16)))()
-    for k, i in enumerate(range(0, count, 16)):
+    # autotuner: block size per graph chosen on every 15th graph of the batch
+    # (both families: the stride is odd)
+    tsample = (fiedler.fiedler_graph * len(range(0, count, 15)))()
+    for k, i in enumerate(range(0, count, 15)):
         tsample[k] = garr[i]
     st, tuning = fiedler.fiedler_plan_autotune(plan.h, tsample)
     if st != fiedler.FIEDLER_OK:
@@ -251,7 +248,8 @@ def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15):
             return None
         return {"max": float(r.max()), "median": float(np.median(r)), "frac_le_1e-5": float((r <= 1e-5).mean()),
                 "graphs": int(r.size)}
-    ms_step = statistics.mean(ms)
+    ms_step = shard.reduce_max(statistics.mean(ms), dist, dev)  # the slowest rank's batch time
+    total = shard.reduce_sum(count, dist, dev)
     nnz = int(sum(g.nnz for g in graphs))
     peak, peak_kind = measured_peaks()
     kgbs = kbytes / (kms / 1e3) / 1e9 if kms > 0 else None
@@ -263,8 +261,8 @@ def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15):
         "workload": batch_name(count), "graphs": count, "vertices": int(sum(g.n for g in graphs)), "nnz": nnz,
         "form": "FP32 values/matvec, FP64 reductions; one persistent launch per call",
         "autotune": {"batch_threads": tuning.batch_threads, "sample_ms_512_256_128": [round(x, 2) for x in tuning.batch_ms],
-                     "sample": f"every 16th graph ({len(tsample)})"},
-        "solves_per_s": count / (ms_step / 1e3), "ms_per_batch": ms_step, "wall_ms_per_batch": 1e3 * statistics.mean(walls),
+                     "sample": f"every 15th graph ({len(tsample)}), repeated to fill the device"},
+        "solves_per_s": total / (ms_step / 1e3), "ms_per_batch": ms_step, "graphs_all_ranks": int(total), "wall_ms_per_batch": 1e3 * statistics.mean(walls),
         "statuses_ok": int((st32 == 0).sum()),
         "kernel": pr_name, "kernel_ms": kms / steps, "gpu_launches_per_batch": launches / steps,
         "kernel_algorithmic_gbs": kgbs, "kernel_frac": (kgbs / peak) if kgbs else None, "peak_kind": f"of {peak_kind}",
@@ -281,7 +279,7 @@ def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15):
 SERVE = dict(rate=2000.0, seconds=3.0, pool=24, nmin=1e3, nmax=2e6, seed=inputs.BASE_SEED + 5)
 
 
-def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"]):
+def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None):
     """The serving form: a Poisson stream of requests at `rate` per second for
     `seconds`, each a graph drawn uniformly from the pool (device-resident
     inputs, copied by fiedler_batch_submit), submitted at its arrival time and
@@ -300,8 +298,9 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"]):
     dgs = [fiedler.device_graph(g, dev) for g in pool]
     plan = fiedler.Plan(stream=stream.cuda_stream, max_batch=256, hbm_budget_bytes=160 << 30,
                         queue_budget_bytes=24 << 30)
-    tsample = (fiedler.fiedler_graph * len(dgs))()
-    for k, (gs, _) in enumerate(dgs):
+    tune = dgs[:16]  # the pool's smaller two thirds (log-spaced sizes up to ~1e5 points), repeated
+    tsample = (fiedler.fiedler_graph * len(tune))()
+    for k, (gs, _) in enumerate(tune):
         tsample[k] = gs
     st, tuning = fiedler.fiedler_plan_autotune(plan.h, tsample)
     if st != fiedler.FIEDLER_OK:
@@ -372,13 +371,14 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"]):
         with cond:
             cond.notify_all()
         plan.close()
-    wall = state["t_last"] - t0
+    wall = shard.reduce_max(state["t_last"] - t0, dist, dev)  # every rank serves its own stream
+    nall = shard.reduce_sum(nreq, dist, dev)
     sizes = np.array([pool[i].n for i in pick])
     return {
         "workload": f"Poisson {rate:g} req/s for {seconds:g} s; kNN mixture graphs, {len(pool)} sizes log-spaced "
                     f"{SERVE['nmin']:g}..{SERVE['nmax']:g} points (largest component kept), seed {seed}",
         "requests": nreq, "completed_ok": int(nreq - state["bad"]), "submit_span_s": t_sub,
-        "submit_retries": retries, "wall_s": wall, "solves_per_s": nreq / wall,
+        "submit_retries": retries, "wall_s": wall, "solves_per_s": nall / wall,
         "p50_ms": 1e3 * float(np.nanpercentile(lat, 50)), "p99_ms": 1e3 * float(np.nanpercentile(lat, 99)),
         "latency": "scheduled arrival to result, client side (includes waiting for queue room)",
         "library_p50_ms": ss.p50_ms, "library_p99_ms": ss.p99_ms,
@@ -389,7 +389,8 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"]):
         "sm_occupancy_est": (ss.block_seconds - base.block_seconds) / wall / max(1, plan_slots),
         "vertices_mean": float(sizes.mean()), "vertices_p99": float(np.percentile(sizes, 99)),
         "form": "FP32 values/matvec, FP64 reductions; continuous batching through a persistent kernel",
-        "autotune": {"batch_threads": tuning.batch_threads, "pool_ms_512_256_128": [round(x, 2) for x in tuning.batch_ms]},
+        "autotune": {"batch_threads": tuning.batch_threads, "sample_ms_512_256_128": [round(x, 2) for x in tuning.batch_ms],
+                     "sample": "the 16 smallest pool graphs, repeated to fill the device"},
         "statuses": {str(k): int(v) for k, v in zip(*np.unique(stats_st, return_counts=True))},
     }
 
@@ -451,7 +452,10 @@ def main():
     batch_graphs = None
     if not args.no_batch and not args.no_extras:
         # generated before CUDA is initialised (worker processes are spawned anyway)
-        batch_graphs = inputs.batch_mix(args.batch_count, seed=BATCH["seed"], procs=min(16, os.cpu_count() or 1))
+        # each rank solves its own share of a batch of (ranks x batch-count) graphs
+        ws0, rank0, _ = dist_env()
+        batch_graphs = inputs.batch_mix(seed=BATCH["seed"], procs=min(16, os.cpu_count() or 1),
+                                        indices=shard.shard_indices(ws0 * args.batch_count, rank0, ws0))
     serve_pool = None
     if not args.no_serve and not args.no_extras:
         serve_pool = inputs.serving_pool(SERVE["pool"], SERVE["nmin"], SERVE["nmax"], SERVE["seed"],
@@ -644,11 +648,12 @@ def main():
                                     "lambda2": ro.lam}
     plan.close()
     if batch_graphs is not None:
-        line["batched"] = batched_leg(batch_graphs, stream, dev)
+        line["batched"] = batched_leg(batch_graphs, stream, dev, dist=dist)
         line["gpu_launches_batched_per_batch"] = line["batched"]["gpu_launches_per_batch"]
         del batch_graphs
     if serve_pool is not None:
-        line["serving"] = serving_leg(serve_pool, stream, dev, args.serve_rate, args.serve_seconds)
+        line["serving"] = serving_leg(serve_pool, stream, dev, args.serve_rate, args.serve_seconds,
+                                      seed=SERVE["seed"] + 7919 * rank, dist=dist)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

@@ -254,7 +254,8 @@ typedef struct {
 
 /* Autotuner of the batched form (a project addition; the paper has none):
  * solves the `count` sample graphs, repeated until every block size has at
- * least two graphs per resident block, as one batch with each block size
+ * least two graphs per resident block (or, for large graphs, until their
+ * memory would pass hbm_budget_bytes), as one batch with each block size
  * (512, 256 and 128 threads per graph, i.e. 1, 2 and 4 graphs resident per
  * SM), keeps the fastest for every later fiedler_solve_batch and serving
  * launch of this plan, and reports the timings of the repeated sample.  Results depend on the block size only

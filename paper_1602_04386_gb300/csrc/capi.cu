@@ -199,10 +199,10 @@ size_t arena_estimate(int64_t n, int64_t nnz, size_t tsz, bool wf64) {
 }
 
 size_t scratch_estimate(int64_t n, int64_t nnz, int nblocks) {
-  // one level's scratch, all live at once: colouring (cround + 3 worklists),
-  // matching (cand + 3 worklists), Galerkin (9 per-vertex / per-aggregate
+  // one level's scratch, all live at once: colouring (cround + 3 worklists +
+  // heavy list), matching (cand + 3 worklists + heavy list), Galerkin (9 per-vertex / per-aggregate
   // arrays, (J, slot) keys + FP64 weights per cross entry), colour histogram
-  double b = 16.0 * n + 16.0 * n + 4.0 * (n + 1) * 9 + 16.0 * nnz + 4.0 * fz::kMaxColors * nblocks +
+  double b = 20.0 * n + 20.0 * n + 4.0 * (n + 1) * 9 + 16.0 * nnz + 4.0 * fz::kMaxColors * nblocks +
              64.0 * 256.0 + (1 << 20);
   return (size_t)b;
 }
@@ -1146,10 +1146,23 @@ fiedler_status fiedler_plan_autotune(fiedler_plan *p, const fiedler_graph *graph
   if (!p || !graphs || count < 1 || p->opt.batch_threads != 0) return FIEDLER_EINVAL;
   std::lock_guard<std::mutex> ex(p->exec_mu);
   // throughput, not the latency of the largest graph: the sample is repeated
-  // until every variant has at least two graphs per resident block
+  // until every variant has at least two graphs per resident block, as far as
+  // the repeated graphs' memory stays within the serving budget (else the
+  // sample as it is, cut to that budget, at least one graph)
   const int type = p->opt.precision == FIEDLER_FP64 ? 0 : 1;
-  int total = count;
-  for (int v = 0; v < 3; v++) total = std::max(total, 2 * p->batch_slots[type][v]);
+  const size_t tsz = type == 0 ? 8 : 4;
+  const size_t budget = p->opt.hbm_budget_bytes ? p->opt.hbm_budget_bytes : (size_t)16 << 30;
+  int want = count;
+  for (int v = 0; v < 3; v++) want = std::max(want, 2 * p->batch_slots[type][v]);
+  int total = 0;
+  size_t bytes = 0;
+  while (total < want) {
+    const fiedler_graph &g = graphs[total % count];
+    const size_t f = item_footprint(g.n, g.nnz, tsz, g.w_dtype == FIEDLER_W_F64);
+    if (total > 0 && bytes + f > budget) break;
+    bytes += f;
+    total++;
+  }
   std::vector<fiedler_result> res((size_t)total);
   BatchCtx &c = p->bsync;
   auto run = [&](int var, float *ms) -> fiedler_status {

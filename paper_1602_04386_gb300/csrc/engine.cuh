@@ -101,8 +101,9 @@ FZD void best_set(Best &b, uint64_t wk, int u, int v) {
 // ---------------------------------------------------------------------------
 // shared storage: a static __shared__ declared in a function is one allocation
 // per kernel
-constexpr int kShSort = 2048;  // u64 words of the raw buffer (16 KB)
+constexpr int kShSort = 2048;  // u64 words of the raw buffer (16 KB); also kWarpSeg per warp
 constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one thread
+constexpr int kWarpSeg = 128;  // longer ones up to this length by one warp (in shared memory)
 constexpr int kHeavyDeg = 32;  // rows of at least this degree are processed by a whole warp
 constexpr int kWarpNnz = 2048;  // tiny levels up to this many entries are smoothed by one warp
 
@@ -111,6 +112,10 @@ FZD uint64_t *sh_raw() {
   return raw;
 }
 FZD int *sh_list() {
+  __shared__ int list[kCtaThreads];
+  return list;
+}
+FZD int *sh_list2() {
   __shared__ int list[kCtaThreads];
   return list;
 }
@@ -123,12 +128,12 @@ FZD long long *sh_ll() {
   return v;
 }
 // heavy vertices (degree >= kHeavyDeg) met by a block in one colouring round
-// or matching phase, deferred to the block's warps; [kHQ] entries, then the
-// count (zero between uses).  0: colouring, 1: matching.
-constexpr int kHQ = 256;
-FZD int *sh_hq(int which) {
-  __shared__ int q[2][kHQ + 1];
-  return q[which];
+// or matching phase are listed (in the block's range of a scratch array) for
+// the block's warps; these are the list lengths (zero between uses).
+// 0: colouring, 1: matching.
+FZD int *sh_hcnt() {
+  __shared__ int c[2];
+  return c;
 }
 FZD double *sh_bc() {  // scalars computed by one thread, read by the block
   __shared__ double v[8];
@@ -308,6 +313,56 @@ FZD void block_bitonic(K *a, int len) {
   }
 }
 
+// the same network run by one warp on a shared-memory segment (len <= 2^k)
+template <class K>
+FZD void warp_bitonic(K *a, int len) {
+  const int lane = threadIdx.x & 31;
+  int P = 1;
+  while (P < len) P <<= 1;
+  for (int k = 2; k <= P; k <<= 1) {
+    const int half = k >> 1;
+    for (int p = lane; p < (P >> 1); p += 32) {
+      int blk = p / half, t = p - blk * half;
+      int i = blk * k + t, j = blk * k + k - 1 - t;
+      if (j < len) {
+        K x = a[i], y = a[j];
+        if (y < x) {
+          a[i] = y;
+          a[j] = x;
+        }
+      }
+    }
+    __syncwarp();
+    for (int jj = k >> 2; jj >= 1; jj >>= 1) {
+      for (int p = lane; p < (P >> 1); p += 32) {
+        int blk = p / jj, t = p - blk * jj;
+        int i = blk * 2 * jj + t, j = i + jj;
+        if (j < len) {
+          K x = a[i], y = a[j];
+          if (y < x) {
+            a[i] = y;
+            a[j] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// sorts g[0, len) (len <= kWarpSeg) by the calling warp, through its slice of
+// the shared raw buffer
+template <class K>
+FZD void warp_sort(K *g, int len) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  K *s = reinterpret_cast<K *>(sh_raw()) + w * kWarpSeg;
+  for (int i = lane; i < len; i += 32) s[i] = g[i];
+  __syncwarp();
+  warp_bitonic(s, len);
+  for (int i = lane; i < len; i += 32) g[i] = s[i];
+  __syncwarp();
+}
+
 template <class K>
 FZD void block_sort(K *g, int len) {
   K *s = reinterpret_cast<K *>(sh_raw());
@@ -337,6 +392,7 @@ struct JPState {
   int active, ready, l, r, n, lo, hi;
   int *cround, *color;
   int *list[3];
+  int *heavy;
   long long visits;
 };
 FZD JPState &jps() {
@@ -667,34 +723,71 @@ struct Eng {
     int lo, hi;
     chunk(n, lo, hi);
     IRed r{0, 0, 0};
+    // entry checks: the column order, the weight, and the mirrored entry (a
+    // binary search in row j for i); light rows one thread each, heavy rows
+    // (degree >= kHeavyDeg) one warp each
+    auto check = [&](int i, int e0, int e, int j, double w) {
+      bool bad = j < 0 || j >= n || (e > e0 && ci[e - 1] >= j) || !isfinite(w) || (j != i && !(w > 0.0));
+      if (!bad && j != i) {
+        int a = rp[j], b = rp[j + 1] - 1, f = -1;
+        while (a <= b) {
+          const int m = (a + b) >> 1, cm = ci[m];
+          if (cm == i) {
+            f = m;
+            break;
+          }
+          if (cm < i) a = m + 1;
+          else b = m - 1;
+        }
+        bad = f < 0 || (wf64 ? wd[f] != wd[e] : wf[f] != wf[e]);
+      }
+      if (bad) {
+        atomicMin((unsigned long long *)&S->bad_index, (unsigned long long)e);
+        fail(ST_EINVAL);
+      }
+      return bad;
+    };
+    {
+      const int lane = threadIdx.x & 31;
+      for (int g0 = lo + (threadIdx.x >> 5) * 32; g0 < hi; g0 += blockDim.x) {
+        const int i0 = g0 + lane;
+        const bool hv = i0 < hi && rp[i0 + 1] - rp[i0] >= kHeavyDeg;
+        unsigned mask = __ballot_sync(0xffffffffu, hv);
+        while (mask) {
+          const int i = g0 + __ffs(mask) - 1;
+          mask &= mask - 1;
+          const int e0 = rp[i], e1 = rp[i + 1];
+          double di = 0.0;
+          int loops = 0;
+          bool bad = false;
+          for (int e = e0 + lane; e < e1; e += 32) {
+            const int j = ci[e];
+            const double w = wf64 ? wd[e] : (double)wf[e];
+            if (validate && check(i, e0, e, j, w)) bad = true;
+            if (j == i) loops++;
+            else di += w;
+          }
+          di = warp_sum(di);
+          loops = warp_sum(loops);
+          bad = __any_sync(0xffffffffu, bad);
+          if (lane == 0 && !bad) {
+            d[i] = di;
+            r.a += e1 - e0 - loops;
+            r.b += loops;
+            r.mx = max(r.mx, (long long)__double_as_longlong(di));
+          }
+        }
+      }
+    }
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       const int e0 = rp[i], e1 = rp[i + 1];
+      if (e1 - e0 >= kHeavyDeg) continue;  // done by a warp above
       double di = 0.0;
       int loops = 0;
       for (int e = e0; e < e1; e++) {
         const int j = ci[e];
         const double w = wf64 ? wd[e] : (double)wf[e];
-        if (validate) {
-          bool bad = j < 0 || j >= n || (e > e0 && ci[e - 1] >= j) || !isfinite(w) || (j != i && !(w > 0.0));
-          if (!bad && j != i) {
-            int a = rp[j], b = rp[j + 1] - 1, f = -1;
-            while (a <= b) {
-              const int m = (a + b) >> 1, cm = ci[m];
-              if (cm == i) {
-                f = m;
-                break;
-              }
-              if (cm < i) a = m + 1;
-              else b = m - 1;
-            }
-            bad = f < 0 || (wf64 ? wd[f] != wd[e] : wf[f] != wf[e]);
-          }
-          if (bad) {
-            atomicMin((unsigned long long *)&S->bad_index, (unsigned long long)e);
-            fail(ST_EINVAL);
-            break;
-          }
-        }
+        if (validate && check(i, e0, e, j, w)) break;
         if (j == i) {
           loops++;
           continue;
@@ -778,8 +871,9 @@ struct Eng {
     int *cround = (int *)salloc(4ull * n);
     int *list[3];
     for (int k = 0; k < 3; k++) list[k] = (int *)salloc(4ull * n);
+    int *heavy = (int *)salloc(4ull * n);
     int *color = (int *)aalloc(4ull * n);
-    if (!cround || !list[0] || !list[1] || !list[2] || !color) return false;
+    if (!cround || !list[0] || !list[1] || !list[2] || !heavy || !color) return false;
     int lo, hi;
     chunk(n, lo, hi);
     int *s_cnt = sh_ints() + 4;  // [0..2] block list counters, [3] block colour max
@@ -790,7 +884,7 @@ struct Eng {
       s_cnt[1] = 0;
       s_cnt[2] = 0;
       s_cnt[3] = -1;
-      sh_hq(0)[kHQ] = 0;
+      sh_hcnt()[0] = 0;
     }
     if (lead()) {
       S->jp_cnt[1] = 0;
@@ -810,6 +904,7 @@ struct Eng {
       jp.cround = cround;
       jp.color = color;
       for (int k = 0; k < 3; k++) jp.list[k] = list[k];
+      jp.heavy = heavy;
       jp.visits = 0;
     }
     __syncthreads();
@@ -829,16 +924,14 @@ struct Eng {
     int *lcur = jp.list[cur], *lnxt = jp.list[nxt];
     // threads in reverse order, so that on small levels the colouring runs on
     // other warps than the step it accompanies
-    int *hq = sh_hq(0);
+    int *hc = sh_hcnt();
+    int *hl = jp.heavy + lo;
     for (int q = blockDim.x - 1 - threadIdx.x; q < cnt; q += blockDim.x) {
       const int v = r == 0 ? lo + q : lcur[lo + q];
       const int e0 = rp[v], e1 = rp[v + 1];
-      if (e1 - e0 >= kHeavyDeg) {  // to the warps, if the queue has room
-        const int k = atomicAdd(&hq[kHQ], 1);
-        if (k < kHQ) {
-          hq[k] = v;
-          continue;
-        }
+      if (e1 - e0 >= kHeavyDeg) {  // to the warps
+        hl[atomicAdd(&hc[0], 1)] = v;
+        continue;
       }
       const uint64_t hv = vtx_hash(v);
       bool top = true;
@@ -878,16 +971,16 @@ struct Eng {
     }
     __syncthreads();
     {
-      const int nh = min(hq[kHQ], kHQ);
+      const int nh = hc[0];
       for (int k = threadIdx.x >> 5; k < nh; k += blockDim.x >> 5)
-        jp_heavy(hq[k], r, rp, ci, cround, color, lnxt + lo, &s_cnt[nxt], &s_cnt[3]);
+        jp_heavy(hl[k], r, rp, ci, cround, color, lnxt + lo, &s_cnt[nxt], &s_cnt[3]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       if (s_cnt[nxt]) atomicAdd(&S->jp_cnt[nxt], s_cnt[nxt]);
       if (s_cnt[3] >= 0) atomicMax(&S->col_max, s_cnt[3]);
       s_cnt[cur] = 0;  // becomes the append target of round r + 2
-      hq[kHQ] = 0;
+      hc[0] = 0;
       jp.visits += cnt;
     }
   }
@@ -1151,16 +1244,18 @@ struct Eng {
     int *cand = (int *)salloc(4ull * n);
     int *list[3];
     for (int k = 0; k < 3; k++) list[k] = (int *)salloc(4ull * n);
-    if (!mate || !cand || !list[0] || !list[1] || !list[2]) return false;
+    int *heavy = (int *)salloc(4ull * n);
+    if (!mate || !cand || !list[0] || !list[1] || !list[2] || !heavy) return false;
     int lo, hi;
     chunk(n, lo, hi);
     int *s_cnt = sh_ints();
-    int *hq = sh_hq(1);
+    int *hc = sh_hcnt();
+    int *hl = heavy + lo;
     if (threadIdx.x == 0) {
       s_cnt[0] = hi - lo;
       s_cnt[1] = 0;
       s_cnt[2] = 0;
-      hq[kHQ] = 0;
+      hc[1] = 0;
     }
     if (lead()) {
       S->wl_cnt[1] = 0;
@@ -1177,12 +1272,9 @@ struct Eng {
       if ((ph & 1) == 0) {  // pick
         for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
           const int v = ph == 0 ? lo + q : list[cur][lo + q];
-          if (rp[v + 1] - rp[v] >= kHeavyDeg) {  // to the warps, if the queue has room
-            const int k = atomicAdd(&hq[kHQ], 1);
-            if (k < kHQ) {
-              hq[k] = v;
-              continue;
-            }
+          if (rp[v + 1] - rp[v] >= kHeavyDeg) {  // to the warps
+            hl[atomicAdd(&hc[1], 1)] = v;
+            continue;
           }
           Best b;
           best_init(b);
@@ -1201,10 +1293,10 @@ struct Eng {
         // heavy vertices: one warp each, lanes over the neighbours, then the
         // warp's best under the same total order (unique, so the merge order
         // does not matter)
-        const int nh = min(hq[kHQ], kHQ);
+        const int nh = hc[1];
         const int lane = threadIdx.x & 31;
         for (int k = threadIdx.x >> 5; k < nh; k += blockDim.x >> 5) {
-          const int v = hq[k];
+          const int v = hl[k];
           Best b;
           best_init(b);
           b.wk = 0;
@@ -1236,7 +1328,7 @@ struct Eng {
       if (threadIdx.x == 0) {
         if (s_cnt[nxt]) atomicAdd(&S->wl_cnt[nxt], s_cnt[nxt]);
         s_cnt[cur] = 0;
-        hq[kHQ] = 0;
+        hc[1] = 0;
       }
       visits += cnt;
       if (!sync_p()) return false;
@@ -1407,11 +1499,18 @@ struct Eng {
     }
     if (!sync_p()) return false;
     // G4: members ascending; offset of each member's entries inside its segment
+    // (short member lists by one thread, medium ones by one warp, long ones by
+    // the whole block)
     {
-      int *s_big = sh_list();
+      int *s_big = sh_list(), *s_mid = sh_list2();
       int &s_nbig = sh_ints()[0];
+      int &s_nmid = sh_ints()[2];
+      const int lane = threadIdx.x & 31;
       for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
-        if (threadIdx.x == 0) s_nbig = 0;
+        if (threadIdx.x == 0) {
+          s_nbig = 0;
+          s_nmid = 0;
+        }
         __syncthreads();
         const int I = t0 + threadIdx.x;
         if (I < hi) {
@@ -1424,8 +1523,30 @@ struct Eng {
               G.memoff[m] = off;
               off += G.cc[m];
             }
+          } else if (len <= kWarpSeg) {
+            s_mid[atomicAdd(&s_nmid, 1)] = I;
           } else {
             s_big[atomicAdd(&s_nbig, 1)] = I;
+          }
+        }
+        __syncthreads();
+        const int nmid = s_nmid;
+        for (int q = threadIdx.x >> 5; q < nmid; q += blockDim.x >> 5) {
+          const int Im = s_mid[q];
+          const int a = G.aggptr[Im], len = G.aggptr[Im + 1] - a;
+          warp_sort(G.members + a, len);
+          int run = 0;
+          for (int k0 = 0; k0 < len; k0 += 32) {
+            const int k = k0 + lane;
+            const int m = k < len ? G.members[a + k] : 0;
+            const int c = k < len ? G.cc[m] : 0;
+            int x = c;
+            for (int o = 1; o < 32; o <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, x, o);
+              if (lane >= o) x += y;
+            }
+            if (k < len) G.memoff[m] = run + x - c;
+            run += __shfl_sync(0xffffffffu, x, 31);
           }
         }
         __syncthreads();
@@ -1463,14 +1584,20 @@ struct Eng {
       }
     }
     if (!sync_p()) return false;
-    // G6: sort each segment by (J, slot); distinct J per coarse row
+    // G6: sort each segment by (J, slot); distinct J per coarse row (short
+    // segments by one thread, medium ones by one warp, long ones by the block)
     red = IRed{0, 0, 0};
     {
-      int *s_big = sh_list();
+      int *s_big = sh_list(), *s_mid = sh_list2();
       int &s_nbig = sh_ints()[0];
       int &s_dist = sh_ints()[1];
+      int &s_nmid = sh_ints()[2];
+      const int lane = threadIdx.x & 31;
       for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
-        if (threadIdx.x == 0) s_nbig = 0;
+        if (threadIdx.x == 0) {
+          s_nbig = 0;
+          s_nmid = 0;
+        }
         __syncthreads();
         const int I = t0 + threadIdx.x;
         if (I < hi) {
@@ -1482,8 +1609,27 @@ struct Eng {
               dcount += (k == 0) || ((G.keys[s + k] >> 32) != (G.keys[s + k - 1] >> 32));
             G.dcnt[I] = dcount;
             red.a += dcount;
+          } else if (len <= kWarpSeg) {
+            s_mid[atomicAdd(&s_nmid, 1)] = I;
           } else {
             s_big[atomicAdd(&s_nbig, 1)] = I;
+          }
+        }
+        __syncthreads();
+        const int nmid = s_nmid;
+        for (int q = threadIdx.x >> 5; q < nmid; q += blockDim.x >> 5) {
+          const int Im = s_mid[q];
+          const int s = G.segptr[Im], len = G.segptr[Im + 1] - s;
+          warp_sort(G.keys + s, len);
+          int dc = 0;
+          for (int k0 = 0; k0 < len; k0 += 32) {
+            const int k = k0 + lane;
+            const bool nw = k < len && ((k == 0) || ((G.keys[s + k] >> 32) != (G.keys[s + k - 1] >> 32)));
+            dc += __popc(__ballot_sync(0xffffffffu, nw));
+          }
+          if (lane == 0) {
+            G.dcnt[Im] = dc;
+            red.a += dc;
           }
         }
         __syncthreads();

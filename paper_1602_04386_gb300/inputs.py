@@ -204,14 +204,15 @@ def _distinct(keys: np.ndarray) -> np.ndarray:
     return s[np.concatenate(([True], s[1:] != s[:-1]))] if s.size else s
 
 
-def largest_component(g: CSR) -> CSR:
-    """Induced subgraph on the largest connected component (vertex order kept)."""
+def largest_component(g: CSR, return_kept: bool = False):
+    """Induced subgraph on the largest connected component (vertex order kept);
+    with return_kept, also the kept original vertex ids."""
     import scipy.sparse as sp
     from scipy.sparse.csgraph import connected_components
     a = sp.csr_matrix((np.ones(g.nnz), g.col, g.rowptr), shape=(g.n, g.n))
     k, lab = connected_components(a, directed=False)
     if k == 1:
-        return g
+        return (g, np.arange(g.n)) if return_kept else g
     big = np.argmax(np.bincount(lab))
     keep = np.flatnonzero(lab == big)
     new = np.full(g.n, -1, np.int64)
@@ -221,7 +222,8 @@ def largest_component(g: CSR) -> CSR:
     r, c, w = new[rows[m]], new[g.col[m]], g.w[m]
     rowptr = np.zeros(keep.size + 1, np.int64)
     rowptr[1:] = np.cumsum(np.bincount(r, minlength=keep.size))
-    return CSR(keep.size, rowptr, c, w, name=g.name + "-lcc")
+    out = CSR(keep.size, rowptr, c, w, name=g.name + "-lcc")
+    return (out, keep) if return_kept else out
 
 
 def rmat(scale: int, edge_factor: int = 8, a=0.57, b=0.19, c=0.19, seed: int = BASE_SEED + 4,
@@ -254,11 +256,12 @@ def rmat(scale: int, edge_factor: int = 8, a=0.57, b=0.19, c=0.19, seed: int = B
 
 
 def knn_mixture(npts: int = 200_000, k: int = 10, clusters: int = 8, sigma: float = 0.5, box: float = 10.0,
-                seed: int = BASE_SEED + 3, dtype=np.float32) -> CSR:
+                seed: int = BASE_SEED + 3, dtype=np.float32, return_labels: bool = False):
     """Points from a mixture of isotropic Gaussians (point i in component
     i mod clusters, means uniform in [0, box]^2, Box-Muller normals), exact
     k-nearest-neighbour graph symmetrised by union, weights exp(-d^2 / 0.25)
-    rounded to f32, largest connected component kept."""
+    rounded to f32, largest connected component kept.  With return_labels,
+    also the mixture component of every kept vertex."""
     from scipy.spatial import cKDTree
     means = uniform01(seed, np.arange(2 * clusters)).reshape(clusters, 2) * box
     u1 = uniform01(seed + 1, np.arange(npts))
@@ -282,7 +285,10 @@ def knn_mixture(npts: int = 200_000, k: int = 10, clusters: int = 8, sigma: floa
     w = np.exp(-dd * dd / 0.25).astype(np.float32)
     w = np.maximum(w, np.float32(np.finfo(np.float32).tiny))  # keep every weight positive
     g = csr_from_edges(npts, lo, hi, w.astype(dtype), dtype=dtype, name=f"knn{npts}-s{seed}")
-    return largest_component(g)
+    if not return_labels:
+        return largest_component(g)
+    g, kept = largest_component(g, return_kept=True)
+    return g, (kept % clusters).astype(np.int64)
 
 
 def batch_mix_item(i: int, seed: int = BASE_SEED + 4, scale_range=(9, 16), side_range=(20, 300)) -> CSR:
@@ -304,11 +310,30 @@ def _batch_items(args):
     return [batch_mix_item(i, seed, scale_range, side_range) for i in range(lo, hi)]
 
 
+def _batch_items_at(args):
+    idx, seed, scale_range, side_range = args
+    return [batch_mix_item(i, seed, scale_range, side_range) for i in idx]
+
+
 def batch_mix(count: int = 4096, seed: int = BASE_SEED + 4, scale_range=(9, 16), side_range=(20, 300),
-              procs: int = 1):
-    """The batched workload: graphs batch_mix_item(0 .. count-1).  With procs > 1
-    they are generated by that many worker processes (started with 'spawn', so
-    this is safe after CUDA has been initialised in the caller)."""
+              procs: int = 1, indices=None):
+    """The batched workload: graphs batch_mix_item(0 .. count-1), or the graphs
+    of the given global indices (one rank's share).  With procs > 1 they are
+    generated by that many worker processes (started with 'spawn', so this is
+    safe after CUDA has been initialised in the caller)."""
+    if indices is not None:
+        idx = list(indices)
+        if procs <= 1 or len(idx) < 64:
+            return [batch_mix_item(i, seed, scale_range, side_range) for i in idx]
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        step = max(1, len(idx) // (8 * procs))
+        parts = [(idx[k:k + step], seed, scale_range, side_range) for k in range(0, len(idx), step)]
+        with cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
+            out = []
+            for part in ex.map(_batch_items_at, parts):
+                out.extend(part)
+        return out
     if procs <= 1 or count < 64:
         return [batch_mix_item(i, seed, scale_range, side_range) for i in range(count)]
     import concurrent.futures as cf
