@@ -116,7 +116,8 @@ typedef struct {
                                 Unit 2-norm, orthogonal to 1, and sign-normalised so that the
                                 entry of largest |x_i| (lowest index on ties) is positive. */
   int x_on_device;           /* 1: x is a device pointer; 0: host pointer */
-  float ms;                  /* device time of the solve (CUDA events) */
+  float ms;                  /* device time of the solve: CUDA events (fiedler_solve), or the
+                                graph's own block time on the device timer (batched form) */
   long long bad_index;       /* first offending position when status == FIEDLER_EINVAL, else -1 */
   fiedler_status status;     /* same value as returned */
 } fiedler_result;
@@ -248,8 +249,10 @@ fiedler_status fiedler_plan_serving_stats(const fiedler_plan *plan, fiedler_serv
 
 typedef struct {
   int batch_threads;         /* block size chosen for this plan's batched and served launches */
-  float batch_ms[3];         /* CUDA-event time of the repeated sample batch with 512, 256
-                                and 128 threads per graph (0 = not measured) */
+  float batch_ms[3];         /* CUDA-event time of the (repeated) sample batch with 512, 256
+                                and 128 threads per graph (0 = not run).  A batch's time is set
+                                both by its total work and by its largest graphs, so the sample
+                                should look like the batches to come (a share of one, say) */
 } fiedler_tuning;
 
 /* Autotuner of the batched form (a project addition; the paper has none):

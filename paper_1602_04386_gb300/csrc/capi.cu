@@ -564,6 +564,9 @@ void batch_collect(BatchCtx &c) {
     r.levels = h->nlevels;
     r.coarsest_n = h->nlevels > 0 ? h->lv[h->coarsest].n : 0;
     r.bad_index = h->bad_index == LLONG_MAX ? -1 : h->bad_index;
+    double ns = 0.0;  // the graph's own device time (its block, device timer)
+    for (int ph = 0; ph < fz::PH_COUNT; ph++) ns += h->phase_ns[1][ph];
+    r.ms = (float)(ns * 1e-6);
     if (out == FIEDLER_OK || out == FIEDLER_ENOTCONVERGED) {
       r.lambda2 = h->lambda;
       r.residual = h->residual;

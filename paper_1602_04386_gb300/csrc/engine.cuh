@@ -104,6 +104,7 @@ FZD void best_set(Best &b, uint64_t wk, int u, int v) {
 constexpr int kShSort = 2048;  // u64 words of the raw buffer (16 KB); also kWarpSeg per warp
 constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one thread
 constexpr int kWarpSeg = 128;  // longer ones up to this length by one warp (in shared memory)
+constexpr int kWarpSegG = 2048;  // longer ones up to this length by one warp in place (global memory)
 constexpr int kHeavyDeg = 32;  // rows of at least this degree are processed by a whole warp
 constexpr int kWarpNnz = 2048;  // tiny levels up to this many entries are smoothed by one warp
 
@@ -244,6 +245,77 @@ FZD void block_dsum(double (&v)[K]) {
   __syncthreads();
 }
 
+// A group of G lanes (G in 4..32, aligned inside the warp) walks the entries
+// [e0, e1) of one heavy row: a head of up to three entries, then aligned
+// quads (each lane loads four column indices and four weights with 16-byte
+// loads; the arrays start on 256-byte boundaries), then the tail.  f(j, w) is
+// called for the lane's entries in a fixed order.
+template <int G, class V, class F>
+FZD void group_row(int e0, int e1, const int *scol, const V *sw, F f) {
+  const int lane = threadIdx.x & (G - 1);
+  const int ea = min(e1, (e0 + 3) & ~3);
+  if (e0 + lane < ea) f(scol[e0 + lane], sw[e0 + lane]);
+  const int nq = (e1 - ea) >> 2;
+#pragma unroll 2
+  for (int q = lane; q < nq; q += G) {
+    const int b = ea + 4 * q;
+    const int4 c = *reinterpret_cast<const int4 *>(scol + b);
+    if constexpr (sizeof(V) == 4) {
+      const float4 w = *reinterpret_cast<const float4 *>(sw + b);
+      f(c.x, (V)w.x);
+      f(c.y, (V)w.y);
+      f(c.z, (V)w.z);
+      f(c.w, (V)w.w);
+    } else {
+      const double2 w0 = *reinterpret_cast<const double2 *>(sw + b);
+      const double2 w1 = *reinterpret_cast<const double2 *>(sw + b + 2);
+      f(c.x, (V)w0.x);
+      f(c.y, (V)w0.y);
+      f(c.z, (V)w1.x);
+      f(c.w, (V)w1.y);
+    }
+  }
+  const int eb = ea + 4 * nq;
+  if (eb + lane < e1) f(scol[eb + lane], sw[eb + lane]);
+}
+template <class V, class F>
+FZD void warp_row(int e0, int e1, const int *scol, const V *sw, F f) {
+  group_row<32>(e0, e1, scol, sw, f);
+}
+
+// sum over an aligned group of G lanes (xor tree); result in every lane of it
+template <int G, class V>
+FZD V group_sum(V v) {
+#pragma unroll
+  for (int o = G >> 1; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int G>
+struct GroupSize {
+  static constexpr int value = G;
+};
+
+// lanes per heavy row from the level's mean heavy-row length: short heavy
+// rows share a warp (more rows in flight), long ones get a whole warp
+FZD int heavy_group(const int *srp, int nl, int n) {
+  const int nh = n - nl;
+  if (nh <= 0) return 32;
+  const int mean = (srp[n] - srp[nl]) / nh;
+  return mean < 128 ? 8 : mean < 512 ? 16 : 32;
+}
+// calls f(GroupSize<G>{}) for the group size g (8, 16 or 32); the grid-wide
+// engine has thousands of warps for the heavy rows and keeps to whole warps
+template <bool GRID, class F>
+FZD void with_group(int g, F f) {
+  if constexpr (GRID) {
+    f(GroupSize<32>{});
+  } else {
+    if (g == 8) f(GroupSize<8>{});
+    else if (g == 16) f(GroupSize<16>{});
+    else f(GroupSize<32>{});
+  }
+}
+
 // warp sum of one value by a fixed xor tree; result in every lane
 template <class V>
 FZD V warp_sum(V v) {
@@ -350,10 +422,15 @@ FZD void warp_bitonic(K *a, int len) {
   }
 }
 
-// sorts g[0, len) (len <= kWarpSeg) by the calling warp, through its slice of
-// the shared raw buffer
+// sorts g[0, len) (len <= kWarpSegG) by the calling warp: through its slice
+// of the shared raw buffer up to kWarpSeg, in place beyond (__syncwarp orders
+// the lanes' global accesses too)
 template <class K>
 FZD void warp_sort(K *g, int len) {
+  if (len > kWarpSeg) {
+    warp_bitonic(g, len);
+    return;
+  }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   K *s = reinterpret_cast<K *>(sh_raw()) + w * kWarpSeg;
   for (int i = lane; i < len; i += 32) s[i] = g[i];
@@ -1447,13 +1524,32 @@ struct Eng {
     const int *rp = L->rowptr, *ci = L->col;
     const int *agg = L->agg;
     const W wl = wof(L);
-    // G1: cross-aggregate entries per fine row and per aggregate
+    // G1: cross-aggregate entries per fine row and per aggregate (heavy rows
+    // by a warp each, found by the warps in groups of 32 rows)
+    const int lane = threadIdx.x & 31, gw = tid >> 5, nwarp = nthr >> 5;
     for (int v = tid; v < n; v += nthr) {
+      if (rp[v + 1] - rp[v] >= kHeavyDeg) continue;
       const int I = agg[v];
       int k = 0;
       for (int e = rp[v]; e < rp[v + 1]; e++) k += agg[ci[e]] != I;
       G.cc[v] = k;
       if (k) atomicAdd(&G.tcnt[I], k);
+    }
+    for (int g0 = gw * 32; g0 < n; g0 += nwarp * 32) {
+      const int v0 = g0 + lane;
+      unsigned mask = __ballot_sync(0xffffffffu, v0 < n && rp[v0 + 1] - rp[v0] >= kHeavyDeg);
+      while (mask) {
+        const int v = g0 + __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int I = agg[v];
+        int k = 0;
+        for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) k += agg[ci[e]] != I;
+        k = warp_sum(k);
+        if (lane == 0) {
+          G.cc[v] = k;
+          if (k) atomicAdd(&G.tcnt[I], k);
+        }
+      }
     }
     if (!sync_p()) return false;
     // G2: member and segment pointers (chunked scans over aggregates)
@@ -1523,7 +1619,7 @@ struct Eng {
               G.memoff[m] = off;
               off += G.cc[m];
             }
-          } else if (len <= kWarpSeg) {
+          } else if (len <= kWarpSegG) {
             s_mid[atomicAdd(&s_nmid, 1)] = I;
           } else {
             s_big[atomicAdd(&s_nbig, 1)] = I;
@@ -1570,8 +1666,10 @@ struct Eng {
       }
     }
     if (!sync_p()) return false;
-    // G5: cross entries into their aggregate's segment, key = (J, slot)
+    // G5: cross entries into their aggregate's segment, key = (J, slot); a
+    // heavy row's slots are handed out in entry order by ballots over chunks
     for (int v = tid; v < n; v += nthr) {
+      if (rp[v + 1] - rp[v] >= kHeavyDeg) continue;
       const int I = agg[v];
       const int base = G.segptr[I];
       int slot = G.memoff[v];
@@ -1581,6 +1679,28 @@ struct Eng {
         G.keys[base + slot] = ((uint64_t)(uint32_t)J << 32) | (uint32_t)slot;
         G.segw[base + slot] = wl[e];
         slot++;
+      }
+    }
+    for (int g0 = gw * 32; g0 < n; g0 += nwarp * 32) {
+      const int v0 = g0 + lane;
+      unsigned mask = __ballot_sync(0xffffffffu, v0 < n && rp[v0 + 1] - rp[v0] >= kHeavyDeg);
+      while (mask) {
+        const int v = g0 + __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int I = agg[v];
+        const int base = G.segptr[I];
+        int slot = G.memoff[v];
+        for (int e0 = rp[v]; e0 < rp[v + 1]; e0 += 32) {
+          const int e = e0 + lane;
+          const int J = e < rp[v + 1] ? agg[ci[e]] : I;
+          const unsigned cross = __ballot_sync(0xffffffffu, J != I);
+          if (J != I) {
+            const int sl = slot + __popc(cross & ((1u << lane) - 1u));
+            G.keys[base + sl] = ((uint64_t)(uint32_t)J << 32) | (uint32_t)sl;
+            G.segw[base + sl] = wl[e];
+          }
+          slot += __popc(cross);
+        }
       }
     }
     if (!sync_p()) return false;
@@ -1609,7 +1729,7 @@ struct Eng {
               dcount += (k == 0) || ((G.keys[s + k] >> 32) != (G.keys[s + k - 1] >> 32));
             G.dcnt[I] = dcount;
             red.a += dcount;
-          } else if (len <= kWarpSeg) {
+          } else if (len <= kWarpSegG) {
             s_mid[atomicAdd(&s_nmid, 1)] = I;
           } else {
             s_big[atomicAdd(&s_nbig, 1)] = I;
@@ -1665,10 +1785,14 @@ struct Eng {
     red = IRed{0, 0, 0};
     {
       long long run = pre;
-      int *s_big = sh_list();
+      int *s_big = sh_list(), *s_mid = sh_list2();
       int &s_nbig = sh_ints()[0];
+      int &s_nmid = sh_ints()[2];
       for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
-        if (threadIdx.x == 0) s_nbig = 0;
+        if (threadIdx.x == 0) {
+          s_nbig = 0;
+          s_nmid = 0;
+        }
         const int I = t0 + threadIdx.x;
         const int dc = I < hi ? G.dcnt[I] : 0;
         int tot;
@@ -1696,8 +1820,43 @@ struct Eng {
             for (int q = crp[I]; q < p; q++) dI += cw[q];
             cd[I] = dI;
             red.mx = max(red.mx, (long long)__double_as_longlong(dI));
+          } else if (len <= kWarpSegG) {
+            s_mid[atomicAdd(&s_nmid, 1)] = I;
           } else {
             s_big[atomicAdd(&s_nbig, 1)] = I;
+          }
+        }
+        __syncthreads();
+        // medium segments: one warp each; group starts found by ballots, each
+        // group summed by the lane at its start in slot order, the diagonal
+        // summed by lane 0 in column order (the same orders as below)
+        const int nmid = s_nmid;
+        for (int qm = threadIdx.x >> 5; qm < nmid; qm += blockDim.x >> 5) {
+          const int Im = s_mid[qm];
+          const int s = G.segptr[Im], len = G.segptr[Im + 1] - s;
+          const int p0 = crp[Im];
+          int gr = 0;
+          for (int k0 = 0; k0 < len; k0 += 32) {
+            const int k = k0 + lane;
+            const bool st = k < len && (k == 0 || (G.keys[s + k] >> 32) != (G.keys[s + k - 1] >> 32));
+            const unsigned sm = __ballot_sync(0xffffffffu, st);
+            if (st) {
+              const uint32_t J = (uint32_t)(G.keys[s + k] >> 32);
+              double sum = 0.0;
+              for (int kk = k; kk < len && (uint32_t)(G.keys[s + kk] >> 32) == J; kk++)
+                sum += G.segw[s + (uint32_t)G.keys[s + kk]];
+              const int pos = p0 + gr + __popc(sm & ((1u << lane) - 1u));
+              ccol[pos] = (int)J;
+              cw[pos] = sum;
+            }
+            gr += __popc(sm);
+          }
+          __syncwarp();
+          if (lane == 0) {
+            double dI = 0.0;
+            for (int q2 = p0; q2 < p0 + gr; q2++) dI += cw[q2];
+            cd[Im] = dI;
+            red.mx = max(red.mx, (long long)__double_as_longlong(dI));
           }
         }
         __syncthreads();
@@ -1885,6 +2044,7 @@ struct Eng {
     const int *srp = L->srowptr, *scol = L->scol, *cst = L->colstart;
     const int lane = threadIdx.x & 31, gw = tid >> 5, nwarp = nthr >> 5;
     const int nl = cst[C];  // light rows [0, nl), heavy rows [nl, n)
+    const int hg = heavy_group(srp, nl, n);
     const V *sw = (const V *)L->sw;
     V *A = (V *)L->x, *B = (V *)L->y;
     const double g = S->opt.guard;
@@ -1921,26 +2081,28 @@ struct Eng {
           acc[0] += (double)xi;
           acc[1] += (double)xi * (double)xi;
         }
-        for (int i = hs + gw; i < he; i += nwarp) {  // heavy rows: one warp each
-          V num = (V)0, dsum = (V)0;
-          const int e1 = srp[i + 1];
-#pragma unroll 4
-          for (int e = srp[i] + lane; e < e1; e += 32) {
-            const int j = scol[e];
-            const V wv = sw[e];
-            const V xj = done(j) ? B[j] : (A[j] - muT) * sT;
-            num += wv * xj;
-            dsum += wv;
+        with_group<GRID>(hg, [&](auto gs) {  // heavy rows: a group of lanes each
+          constexpr int G = decltype(gs)::value, GW = 32 / G;
+          const int gl = lane & (G - 1), gi = lane / G;
+          for (int base = hs + gw * GW; base < he; base += nwarp * GW) {
+            const int i = base + gi;
+            V num = (V)0, dsum = (V)0;
+            if (i < he)
+              group_row<G>(srp[i], srp[i + 1], scol, sw, [&](int j, V wv) {
+                const V xj = done(j) ? B[j] : (A[j] - muT) * sT;
+                num += wv * xj;
+                dsum += wv;
+              });
+            num = group_sum<G>(num);
+            dsum = group_sum<G>(dsum);
+            if (gl == 0 && i < he) {
+              const V xi = num / dsum;
+              B[i] = xi;
+              acc[0] += (double)xi;
+              acc[1] += (double)xi * (double)xi;
+            }
           }
-          num = warp_sum(num);
-          dsum = warp_sum(dsum);
-          const V xi = num / dsum;
-          if (lane == 0) {
-            B[i] = xi;
-            acc[0] += (double)xi;
-            acc[1] += (double)xi * (double)xi;
-          }
-        }
+        });
         if (c + 1 < C && !sync()) return false;
       }
       if (!grid_dsum<2>(acc)) return false;
@@ -1998,15 +2160,21 @@ struct Eng {
         for (int e = srp[i]; e < e1; e++) lx += sw[e] * (xi - A[scol[e]]);
         row(i, xi, lx);
       }
-      for (int i = nl + gw; i < n; i += nwarp) {
-        const V xi = A[i];
-        V lx = (V)0;
-        const int e1 = srp[i + 1];
-#pragma unroll 4
-        for (int e = srp[i] + lane; e < e1; e += 32) lx += sw[e] * (xi - A[scol[e]]);
-        lx = warp_sum(lx);
-        if (lane == 0) row(i, xi, lx);
-      }
+      with_group<GRID>(hg, [&](auto gs) {
+        constexpr int G = decltype(gs)::value, GW = 32 / G;
+        const int gl = lane & (G - 1), gi = lane / G;
+        // the bound is uniform in the warp: every lane reaches the group sums
+        for (int base = nl + gw * GW; base < n; base += nwarp * GW) {
+          const int i = base + gi;
+          V xi = (V)0, lx = (V)0;
+          if (i < n) {
+            xi = A[i];
+            group_row<G>(srp[i], srp[i + 1], scol, sw, [&](int j, V wv) { lx += wv * (xi - A[j]); });
+          }
+          lx = group_sum<G>(lx);
+          if (gl == 0 && i < n) row(i, xi, lx);
+        }
+      });
       if (!grid_dsum<4>(acc)) return false;
       if (resid && !grid_dsum<2>(acr)) return false;
       FZ_MARK(ph_pi, sweep_bytes);
@@ -2270,21 +2438,26 @@ struct Eng {
         }
         row(xi, lx, num);
       }
-      for (int k = nl + gw; k < n; k += nwarp) {  // heavy rows: one warp each
-        const V xi = A[k];
-        V lx = (V)0, num = (V)0;
-        const int e1 = srp[k + 1];
-#pragma unroll 4
-        for (int e = srp[k] + lane; e < e1; e += 32) {
-          const V dl = xi - A[scol[e]];
-          const V wd = sw[e] * dl;
-          lx += wd;
-          num += wd * dl;
+      with_group<GRID>(heavy_group(srp, nl, n), [&](auto gs) {  // heavy rows: a group of lanes each
+        constexpr int G = decltype(gs)::value, GW = 32 / G;
+        const int gl = lane & (G - 1), gi = lane / G;
+        for (int base = nl + gw * GW; base < n; base += nwarp * GW) {
+          const int k = base + gi;
+          V xi = (V)0, lx = (V)0, num = (V)0;
+          if (k < n) {
+            xi = A[k];
+            group_row<G>(srp[k], srp[k + 1], scol, sw, [&](int j, V wv) {
+              const V dl = xi - A[j];
+              const V wd = wv * dl;
+              lx += wd;
+              num += wd * dl;
+            });
+          }
+          lx = group_sum<G>(lx);
+          num = group_sum<G>(num);
+          if (gl == 0 && k < n) row(xi, lx, num);
         }
-        lx = warp_sum(lx);
-        num = warp_sum(num);
-        if (lane == 0) row(xi, lx, num);
-      }
+      });
     }
     if (!grid_dsum<4>(acc)) return false;
     acc[2] *= s * s;
