@@ -1049,8 +1049,16 @@ struct Eng {
     __syncthreads();
     {
       const int nh = hc[0];
-      for (int k = threadIdx.x >> 5; k < nh; k += blockDim.x >> 5)
-        jp_heavy(hl[k], r, rp, ci, cround, color, lnxt + lo, &s_cnt[nxt], &s_cnt[3]);
+      const int mean = L->nnz / (L->n > 0 ? L->n : 1);
+      with_group<GRID>(mean < 128 ? 8 : mean < 512 ? 16 : 32, [&](auto gs) {
+        constexpr int G = decltype(gs)::value, GW = 32 / G;
+        const int gi = (threadIdx.x & 31) / G;
+        for (int kb = (threadIdx.x >> 5) * GW; kb < nh; kb += (blockDim.x >> 5) * GW) {
+          const int k = kb + gi;
+          const bool valid = k < nh;
+          jp_heavy_g<G>(valid ? hl[k] : 0, valid, r, rp, ci, cround, color, lnxt + lo, &s_cnt[nxt], &s_cnt[3]);
+        }
+      });
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1062,53 +1070,73 @@ struct Eng {
     }
   }
 
-  // One heavy vertex's colouring round, by a whole warp: the same decision as
-  // the one-thread path (top priority among the neighbours uncoloured at the
-  // start of round r; smallest colour unused by neighbours coloured earlier),
-  // with the neighbour scans split across the lanes.
-  FZD static void jp_heavy(int v, int r, const int *rp, const int *ci, int *cround, int *color, int *lnxt,
-                           int *cnt_nxt, int *cmax) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t hv = vtx_hash(v);
-    const int e0 = rp[v], e1 = rp[v + 1];
-    for (int b = e0; b < e1; b += 32) {
-      const int e = b + lane;
+  // One heavy vertex's colouring round, by an aligned group of G lanes
+  // (several vertices in flight per warp): the same decision as the
+  // one-thread path (top priority among the neighbours uncoloured at the start
+  // of round r; smallest colour unused by neighbours coloured earlier), with
+  // the neighbour scans split across the group.  Every lane of the warp calls it
+  // (valid = false for lanes without a vertex); the loops run until no group
+  // in the warp has work left, so the warp-wide votes see every lane.
+  template <int G>
+  FZD static void jp_heavy_g(int v, bool valid, int r, const int *rp, const int *ci, int *cround, int *color,
+                             int *lnxt, int *cnt_nxt, int *cmax) {
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1));
+    const uint64_t hv = valid ? vtx_hash(v) : 0;
+    const int e0 = valid ? rp[v] : 0, e1 = valid ? rp[v + 1] : 0;
+    bool active = valid && e0 < e1, beaten = false;
+    int b = e0;
+    while (__any_sync(0xffffffffu, active)) {
       bool beat = false;
-      if (e < e1) {
-        const int u = ci[e];
-        if (cround[u] >= r) {
-          const uint64_t hu = vtx_hash(u);
-          beat = hu > hv || (hu == hv && u > v);
+      if (active) {
+        const int e = b + gl;
+        if (e < e1) {
+          const int u = ci[e];
+          if (cround[u] >= r) {
+            const uint64_t hu = vtx_hash(u);
+            beat = hu > hv || (hu == hv && u > v);
+          }
         }
       }
-      if (__any_sync(0xffffffffu, beat)) {
-        if (lane == 0) lnxt[atomicAdd(cnt_nxt, 1)] = v;
-        return;
-      }
-    }
-    int base = 0, c = 0;
-    for (;;) {
-      uint64_t m = 0;
-      for (int e = e0 + lane; e < e1; e += 32) {
-        const int u = ci[e];
-        if (cround[u] < r) {
-          const int cu = color[u] - base;
-          if (cu >= 0 && cu < 64) m |= 1ull << cu;
+      const unsigned bal = __ballot_sync(0xffffffffu, beat) & gmask;
+      if (active) {
+        if (bal) {
+          beaten = true;
+          active = false;
+        } else {
+          b += G;
+          active = b < e1;
         }
       }
-      const unsigned mlo = __reduce_or_sync(0xffffffffu, (unsigned)m);
-      const unsigned mhi = __reduce_or_sync(0xffffffffu, (unsigned)(m >> 32));
-      m = ((uint64_t)mhi << 32) | mlo;
-      if (m != ~0ull) {
-        c = base + __ffsll((long long)~m) - 1;
-        break;
-      }
-      base += 64;
     }
-    if (lane == 0) {
-      color[v] = c;
-      cround[v] = r;
-      atomicMax(cmax, c);
+    if (valid && beaten && gl == 0) lnxt[atomicAdd(cnt_nxt, 1)] = v;
+    bool need = valid && !beaten;
+    int base = 0;
+    while (__any_sync(0xffffffffu, need)) {
+      unsigned long long m = 0;
+      if (need)
+        for (int e = e0 + gl; e < e1; e += G) {
+          const int u = ci[e];
+          if (cround[u] < r) {
+            const int cu = color[u] - base;
+            if (cu >= 0 && cu < 64) m |= 1ull << cu;
+          }
+        }
+#pragma unroll
+      for (int o = G >> 1; o >= 1; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+      if (need) {
+        if (m != ~0ull) {
+          const int c = base + __ffsll((long long)~m) - 1;
+          need = false;
+          if (gl == 0) {
+            color[v] = c;
+            cround[v] = r;
+            atomicMax(cmax, c);
+          }
+        } else {
+          base += 64;
+        }
+      }
     }
   }
 
@@ -1372,27 +1400,34 @@ struct Eng {
         // does not matter)
         const int nh = hc[1];
         const int lane = threadIdx.x & 31;
-        for (int k = threadIdx.x >> 5; k < nh; k += blockDim.x >> 5) {
-          const int v = hl[k];
-          Best b;
-          best_init(b);
-          b.wk = 0;
-          for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
-            const int u = ci[e];
-            if (ph > 0 && mate[u] >= 0) continue;
-            const uint64_t wk = wl.key(e);
-            if (best_beats(b, wk, v, u, tie)) best_set(b, wk, v, u);
+        const int mean = L->nnz / (n > 0 ? n : 1);
+        with_group<GRID>(mean < 128 ? 8 : mean < 512 ? 16 : 32, [&](auto gs) {
+          constexpr int G = decltype(gs)::value, GW = 32 / G;
+          const int gl = lane & (G - 1), gi = lane / G;
+          for (int kb = (threadIdx.x >> 5) * GW; kb < nh; kb += (blockDim.x >> 5) * GW) {
+            const int k = kb + gi;
+            const int v = k < nh ? hl[k] : 0;
+            Best b;
+            best_init(b);
+            b.wk = 0;
+            if (k < nh)
+              for (int e = rp[v] + gl; e < rp[v + 1]; e += G) {
+                const int u = ci[e];
+                if (ph > 0 && mate[u] >= 0) continue;
+                const uint64_t wk = wl.key(e);
+                if (best_beats(b, wk, v, u, tie)) best_set(b, wk, v, u);
+              }
+            for (int o = G >> 1; o >= 1; o >>= 1) {
+              const uint64_t owk = __shfl_xor_sync(0xffffffffu, b.wk, o);
+              const int ov = __shfl_xor_sync(0xffffffffu, b.v, o);
+              if (ov >= 0 && best_beats(b, owk, v, ov, tie)) best_set(b, owk, v, ov);
+            }
+            if (k < nh && gl == 0 && b.v >= 0) {
+              cand[v] = b.v;
+              list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
+            }
           }
-          for (int o = 16; o >= 1; o >>= 1) {
-            const uint64_t owk = __shfl_xor_sync(0xffffffffu, b.wk, o);
-            const int ov = __shfl_xor_sync(0xffffffffu, b.v, o);
-            if (ov >= 0 && best_beats(b, owk, v, ov, tie)) best_set(b, owk, v, ov);
-          }
-          if (lane == 0 && b.v >= 0) {
-            cand[v] = b.v;
-            list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
-          }
-        }
+        });
       } else {  // match
         for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
           const int v = list[cur][lo + q];
