@@ -438,7 +438,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp64 / cpu baseline legs (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e / fp64 / cpu baseline legs")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form leg")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"])
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-form leg")
@@ -450,14 +450,14 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     batch_graphs = None
-    if not args.no_batch and not args.no_extras:
+    if not args.no_batch:
         # generated before CUDA is initialised (worker processes are spawned anyway)
         # each rank solves its own share of a batch of (ranks x batch-count) graphs
         ws0, rank0, _ = dist_env()
         batch_graphs = inputs.batch_mix(seed=BATCH["seed"], procs=min(16, os.cpu_count() or 1),
                                         indices=shard.shard_indices(ws0 * args.batch_count, rank0, ws0))
     serve_pool = None
-    if not args.no_serve and not args.no_extras:
+    if not args.no_serve:
         serve_pool = inputs.serving_pool(SERVE["pool"], SERVE["nmin"], SERVE["nmax"], SERVE["seed"],
                                          procs=min(16, os.cpu_count() or 1))
 
