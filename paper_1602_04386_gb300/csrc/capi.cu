@@ -200,9 +200,9 @@ size_t arena_estimate(int64_t n, int64_t nnz, size_t tsz, bool wf64) {
 
 size_t scratch_estimate(int64_t n, int64_t nnz, int nblocks) {
   // one level's scratch, all live at once: colouring (cround + 3 worklists +
-  // heavy list), matching (cand + 3 worklists + heavy list), Galerkin (9 per-vertex / per-aggregate
+  // heavy list + resume positions), matching (cand + 3 worklists + heavy list), Galerkin (9 per-vertex / per-aggregate
   // arrays, (J, slot) keys + FP64 weights per cross entry), colour histogram
-  double b = 20.0 * n + 20.0 * n + 4.0 * (n + 1) * 9 + 16.0 * nnz + 4.0 * fz::kMaxColors * nblocks +
+  double b = 24.0 * n + 20.0 * n + 4.0 * (n + 1) * 9 + 16.0 * nnz + 4.0 * fz::kMaxColors * nblocks +
              64.0 * 256.0 + (1 << 20);
   return (size_t)b;
 }

@@ -106,6 +106,7 @@ constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one t
 constexpr int kWarpSeg = 128;  // longer ones up to this length by one warp (in shared memory)
 constexpr int kWarpSegG = 2048;  // longer ones up to this length by one warp in place (global memory)
 constexpr int kHeavyDeg = 32;  // rows of at least this degree are processed by a whole warp
+constexpr int kJposDeg = 16;   // colouring: vertices of at least this degree remember their blocker
 constexpr int kWarpNnz = 2048;  // tiny levels up to this many entries are smoothed by one warp
 
 FZD uint64_t *sh_raw() {
@@ -470,6 +471,7 @@ struct JPState {
   int *cround, *color;
   int *list[3];
   int *heavy;
+  int *jpos;  // per blocked vertex: position of the neighbour that last blocked it
   long long visits;
 };
 FZD JPState &jps() {
@@ -949,8 +951,9 @@ struct Eng {
     int *list[3];
     for (int k = 0; k < 3; k++) list[k] = (int *)salloc(4ull * n);
     int *heavy = (int *)salloc(4ull * n);
+    int *jpos = (int *)salloc(4ull * n);
     int *color = (int *)aalloc(4ull * n);
-    if (!cround || !list[0] || !list[1] || !list[2] || !heavy || !color) return false;
+    if (!cround || !list[0] || !list[1] || !list[2] || !heavy || !jpos || !color) return false;
     int lo, hi;
     chunk(n, lo, hi);
     int *s_cnt = sh_ints() + 4;  // [0..2] block list counters, [3] block colour max
@@ -982,6 +985,7 @@ struct Eng {
       jp.color = color;
       for (int k = 0; k < 3; k++) jp.list[k] = list[k];
       jp.heavy = heavy;
+      jp.jpos = jpos;
       jp.visits = 0;
     }
     __syncthreads();
@@ -1010,9 +1014,15 @@ struct Eng {
         hl[atomicAdd(&hc[0], 1)] = v;
         continue;
       }
+      // a blocked vertex of degree >= kJposDeg resumes its scan at the
+      // neighbour that blocked it: the neighbours before it had lower priority
+      // or were coloured, and stay so, so only that one and the later ones can
+      // block it now (short rows are cheaper to rescan than to remember)
       const uint64_t hv = vtx_hash(v);
       bool top = true;
-      for (int e = e0; e < e1; e++) {
+      const bool keep = e1 - e0 >= kJposDeg;
+      int e = (r == 0 || !keep) ? e0 : jp.jpos[v];
+      for (; e < e1; e++) {
         const int u = ci[e];
         if (cround[u] >= r) {
           const uint64_t hu = vtx_hash(u);
@@ -1023,6 +1033,7 @@ struct Eng {
         }
       }
       if (!top) {
+        if (keep) jp.jpos[v] = e;
         lnxt[lo + atomicAdd(&s_cnt[nxt], 1)] = v;
         continue;
       }
@@ -1056,7 +1067,8 @@ struct Eng {
         for (int kb = (threadIdx.x >> 5) * GW; kb < nh; kb += (blockDim.x >> 5) * GW) {
           const int k = kb + gi;
           const bool valid = k < nh;
-          jp_heavy_g<G>(valid ? hl[k] : 0, valid, r, rp, ci, cround, color, lnxt + lo, &s_cnt[nxt], &s_cnt[3]);
+          jp_heavy_g<G>(valid ? hl[k] : 0, valid, r, rp, ci, cround, color, jp.jpos, lnxt + lo, &s_cnt[nxt],
+                        &s_cnt[3]);
         }
       });
     }
@@ -1079,13 +1091,13 @@ struct Eng {
   // in the warp has work left, so the warp-wide votes see every lane.
   template <int G>
   FZD static void jp_heavy_g(int v, bool valid, int r, const int *rp, const int *ci, int *cround, int *color,
-                             int *lnxt, int *cnt_nxt, int *cmax) {
-    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
-    const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1));
+                             int *jpos, int *lnxt, int *cnt_nxt, int *cmax) {
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1), g0 = lane & ~(G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << g0;
     const uint64_t hv = valid ? vtx_hash(v) : 0;
     const int e0 = valid ? rp[v] : 0, e1 = valid ? rp[v + 1] : 0;
-    bool active = valid && e0 < e1, beaten = false;
-    int b = e0;
+    int b = valid ? (r == 0 ? e0 : jpos[v]) : 0;  // resume at the last blocker (see jp_round)
+    bool active = valid && b < e1, beaten = false;
     while (__any_sync(0xffffffffu, active)) {
       bool beat = false;
       if (active) {
@@ -1103,6 +1115,7 @@ struct Eng {
         if (bal) {
           beaten = true;
           active = false;
+          if (gl == 0) jpos[v] = b + __ffs(bal >> g0) - 1;  // the first blocker of the chunk
         } else {
           b += G;
           active = b < e1;
