@@ -1390,6 +1390,12 @@ struct Eng {
       if ((ph & 1) == 0) {  // pick
         for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
           const int v = ph == 0 ? lo + q : list[cur][lo + q];
+          if (ph > 0 && mate[cand[v]] < 0) {
+            // the best free neighbour of the last pick is still free, and the
+            // free set only shrinks, so it is still the best: no rescan
+            list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
+            continue;
+          }
           if (rp[v + 1] - rp[v] >= kHeavyDeg) {  // to the warps
             hl[atomicAdd(&hc[1], 1)] = v;
             continue;
