@@ -302,7 +302,7 @@ FZD int heavy_group(const int *srp, int nl, int n) {
   const int nh = n - nl;
   if (nh <= 0) return 32;
   const int mean = (srp[n] - srp[nl]) / nh;
-  return mean < 128 ? 8 : mean < 512 ? 16 : 32;
+  return mean < 1024 ? 8 : mean < 4096 ? 16 : 32;
 }
 // calls f(GroupSize<G>{}) for the group size g (8, 16 or 32); the grid-wide
 // engine has thousands of warps for the heavy rows and keeps to whole warps
