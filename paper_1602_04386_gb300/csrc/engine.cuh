@@ -107,7 +107,7 @@ constexpr int kWarpSeg = 128;  // longer ones up to this length by one warp (in 
 constexpr int kWarpSegG = 2048;  // longer ones up to this length by one warp in place (global memory)
 constexpr int kHeavyDeg = 32;  // rows of at least this degree are processed by a whole warp
 constexpr int kJposDeg = 16;   // colouring: vertices of at least this degree remember their blocker
-constexpr int kWarpNnz = 2048;  // tiny levels up to this many entries are smoothed by one warp
+constexpr int kWarpNnz = 512;  // tiny levels up to this many entries are smoothed by one warp
 
 FZD uint64_t *sh_raw() {
   __shared__ uint64_t raw[kShSort];
