@@ -43,6 +43,8 @@ struct Ticket {
   double *x = nullptr;  // device result vector
   size_t footprint = 0;  // device bytes while in flight (admission)
   double scale = 1.0;     // arena / scratch estimate factor (doubled on a rerun)
+  double learn = 1.0;     // the plan's learned arena factor when it was admitted
+  size_t arena_b = 0, scratch_b = 0;  // its allocation at admission
   char *dwork = nullptr;  // in flight: state | arena | scratch (pool allocation)
   unsigned long long k = 0;  // position in the serving ring
   std::chrono::steady_clock::time_point t_submit;
@@ -155,6 +157,12 @@ struct fiedler_plan {
   uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, n_batched_tickets = 0;
   std::vector<float> latencies_ms;
   double block_seconds = 0.0, live_sum = 0.0, alive_sum = 0.0;
+  // serving admission learns how much of the arena estimate tickets use: the
+  // largest (arena used / estimate) seen, times 1.25, bounds later estimates
+  double arena_ratio = 0.0;
+  double arena_factor() const {
+    return arena_ratio <= 0.0 ? 1.0 : std::min(1.0, std::max(0.25, 1.25 * arena_ratio));
+  }
   uint64_t live_rounds = 0;
 };
 
@@ -744,12 +752,16 @@ void worker_main(fiedler_plan *p) {
           cudaFreeAsync(t->dwork, p->io_stream);
           t->dwork = nullptr;
           p->inflight_bytes -= t->footprint;
+          if (ok && h->status == fz::ST_ARENA) p->arena_ratio = std::max(p->arena_ratio, 2.0 * t->learn);
           if (ok && (h->status == fz::ST_ARENA || h->status == fz::ST_SCRATCH) && t->scale < 8.0) {
             t->scale *= 2.0;  // the hierarchy outgrew its estimate: run it again with more room
             t->running = false;
             p->queue.push_front(t->id);
             continue;
           }
+          if (ok && h->status == fz::ST_OK)
+            p->arena_ratio = std::max(p->arena_ratio, (double)h->arena_off / (double)arena_estimate(
+                                                          t->n, t->nnz, tsz, t->w_dtype == FIEDLER_W_F64));
           if (ok) ticket_result(h, t);
           else t->st = FIEDLER_ECUDA;
           if (ok)
@@ -782,6 +794,11 @@ void worker_main(fiedler_plan *p) {
           p->q_cv.notify_all();
           continue;
         }
+        // footprint with the learned arena factor (a rerun doubles t->scale)
+        t->learn = p->arena_factor();
+        t->arena_b = r256((size_t)(arena_estimate(t->n, t->nnz, tsz, t->w_dtype == FIEDLER_W_F64) * t->scale * t->learn));
+        t->scratch_b = r256((size_t)(scratch_estimate(t->n, t->nnz, 1) * t->scale));
+        t->footprint = r256(sizeof(State)) + t->arena_b + t->scratch_b;
         const bool empty = p->inflight_bytes == 0 && adm.empty();
         if (!empty && p->inflight_bytes + t->footprint > budget) break;  // wait for memory to free up
         p->queue.pop_front();
@@ -796,8 +813,7 @@ void worker_main(fiedler_plan *p) {
       int staged = 0;
       std::vector<Ticket *> ok_t;
       for (Ticket *t : adm) {
-        const size_t ab = r256((size_t)(arena_estimate(t->n, t->nnz, tsz, t->w_dtype == FIEDLER_W_F64) * t->scale));
-        const size_t sb = r256((size_t)(scratch_estimate(t->n, t->nnz, 1) * t->scale));
+        const size_t ab = t->arena_b, sb = t->scratch_b;
         const size_t bytes = r256(sizeof(State)) + ab + sb;
         if (cudaMallocFromPoolAsync((void **)&t->dwork, bytes, p->pool, p->io_stream) != cudaSuccess) {
           t->dwork = nullptr;
