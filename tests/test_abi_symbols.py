@@ -61,6 +61,8 @@ int main(void){
  printf("%zu %zu %zu %zu\n", offsetof(fiedler_options, seed), offsetof(fiedler_result, x),
         offsetof(fiedler_result, bad_index), offsetof(fiedler_profile, phase_bytes));
  printf("%zu\n", offsetof(fiedler_level_info, phase_ms));
+ printf("%zu %zu %zu %zu\n", sizeof(fiedler_tuning), sizeof(fiedler_serving_stats),
+        offsetof(fiedler_serving_stats, mean_blocks), offsetof(fiedler_options, batch_threads));
  return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
@@ -72,6 +74,9 @@ int main(void){
     sizes = [int(v) for v in out[:5]]
     offs = [int(v) for v in out[5:9]]
     assert int(out[9]) == fiedler.fiedler_level_info.phase_ms.offset
+    assert [int(v) for v in out[10:14]] == [C.sizeof(fiedler.fiedler_tuning), C.sizeof(fiedler.fiedler_serving_stats),
+                                             fiedler.fiedler_serving_stats.mean_blocks.offset,
+                                             fiedler.fiedler_options.batch_threads.offset]
     assert sizes == [C.sizeof(fiedler.fiedler_options), C.sizeof(fiedler.fiedler_graph),
                      C.sizeof(fiedler.fiedler_result), C.sizeof(fiedler.fiedler_level_info),
                      C.sizeof(fiedler.fiedler_profile)]
