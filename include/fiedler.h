@@ -146,13 +146,14 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
  * EDEGENERATE; ENOTCONVERGED still fills the result. */
 fiedler_status fiedler_solve(fiedler_plan *plan, const fiedler_graph *graph, fiedler_result *result);
 
-/* Batched form: solves `count` independent graphs in one persistent launch
- * (each graph by one thread block running every level of its hierarchy;
- * blocks take the next graph when they finish one).  results[i] is filled as
- * by fiedler_solve (results[i].x / x_on_device give the output buffer, may be
- * NULL); a graph's result does not depend on the other graphs of the batch.
- * Returns FIEDLER_OK if the batch ran (per-graph outcomes in results[i].status),
- * or the error that stopped it. */
+/* Batched form (a project addition): solves `count` independent graphs in one
+ * persistent launch (each graph by one thread block of batch_threads threads
+ * running every level of its hierarchy; blocks take the next graph, largest
+ * first, when they finish one).  results[i] is filled as by fiedler_solve
+ * (results[i].x / x_on_device give the output buffer, may be NULL; ms is the
+ * graph's own device time); a graph's result does not depend on the other
+ * graphs of the batch.  Returns FIEDLER_OK if the batch ran (per-graph outcomes
+ * in results[i].status), or the error that stopped it. */
 fiedler_status fiedler_solve_batch(fiedler_plan *plan, const fiedler_graph *graphs, int count,
                                    fiedler_result *results);
 

@@ -84,7 +84,7 @@ def test_batch_invalid_members_do_not_stop_the_batch():
 
 def test_serving_tickets_alone_and_in_the_mix():
     """Tickets submitted in waves while earlier ones are on the GPU (admitted
-    as memory and launch slots free up) give the same result as alone."""
+    as memory and blocks free up) give the same result as alone."""
     gs = mixed_grids(24, seed=5)
     want = [alone(g, fiedler.FIEDLER_FP32_FP64RED) for g in gs]
     with fiedler.Plan(max_batch=5) as p:
