@@ -25,8 +25,8 @@ def setup_module(module):
     fiedler.load()
 
 
-def check_against_oracle(g, precision, lam_tol, tail=4096):
-    with fiedler.Plan(precision=precision, tail_max_n=tail) as p:
+def check_against_oracle(g, precision, lam_tol, tail=4096, tail_nnz=32768):
+    with fiedler.Plan(precision=precision, tail_max_n=tail, tail_max_nnz=tail_nnz) as p:
         r = p.solve(g)
         assert r.status in (fiedler.FIEDLER_OK, fiedler.FIEDLER_ENOTCONVERGED), r
         counts = [p.level_info(l).pi_iters for l in range(p.num_levels)]
@@ -66,3 +66,27 @@ def test_batch_mix_equals_single_solves():
             a = q.solve(g)
         assert r.status == a.status == fiedler.FIEDLER_OK
         assert r.lambda2 == a.lambda2 and np.array_equal(r.x, a.x)
+
+
+def test_knn_full_size_fp32():
+    """The spectral-clustering workload at its full size (200,000 points, FP32
+    form as the benchmark runs it): hierarchy bit for bit on every level, lambda_2
+    within 1e-5 of the oracle run with the GPU's per-level iteration counts."""
+    g = inputs.knn_mixture(200000)
+    r = check_against_oracle(g, FP32, 1e-5)
+    assert abs(np.linalg.norm(r.x) - 1) < 1e-9 and r.ortho < 1e-9
+
+
+def test_batch_workload_sample():
+    """Graphs of the 4096-graph batched workload solved in a batch with 29
+    others (among them scale-16 R-MAT graphs, the largest): each equals its
+    own one-block solve bit for bit, and that solve matches the oracle."""
+    sample = [0, 1, 2, 15, 17, 37]  # grids and R-MAT graphs; 15, 17 and 37 are scale 16
+    others = list(range(100, 124))
+    gs = inputs.batch_mix(indices=sample + others)
+    with fiedler.Plan() as p:
+        res = p.solve_batch(gs)
+    for g, r in zip(gs[:len(sample)], res[:len(sample)]):
+        assert r.status == fiedler.FIEDLER_OK
+        a = check_against_oracle(g, FP32, 1e-5, tail=1 << 30, tail_nnz=1 << 30)
+        assert r.lambda2 == a.lambda2
