@@ -287,11 +287,12 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None)
     """The serving form: a Poisson stream of requests at `rate` per second for
     `seconds`, each a graph drawn uniformly from the pool (device-resident
     inputs, copied by fiedler_batch_submit), submitted at its arrival time and
-    polled by a second thread; the plan's continuous batching admits tickets by
-    their device-memory footprint.  When the queue budget is used up the
-    submitter waits and retries (back-pressure), so a request's latency is
-    taken from its scheduled arrival to the poll that returns its result (the
-    poller takes finished tickets in any order).
+    collected by a second thread as fiedler_poll_any lists them; the plan's
+    continuous batching admits tickets by their device-memory footprint.  When
+    submit answers EAGAIN (queue budget used up, or device memory held by
+    earlier tickets) the submitter waits and retries (back-pressure), so a
+    request's latency is taken from its scheduled arrival to the poll that
+    returns its result (tickets are collected in the order they finish).
     Throughput is completions over first arrival to last completion."""
     import threading
     import torch
@@ -303,7 +304,7 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None)
     dgs = [fiedler.device_graph(g, dev) for g in pool]
     torch.cuda.empty_cache()  # earlier legs' cached blocks back to the device
     plan = fiedler.Plan(stream=stream.cuda_stream, max_batch=256, hbm_budget_bytes=200 << 30,
-                        queue_budget_bytes=32 << 30)
+                        queue_budget_bytes=8 << 30)
     tune = dgs[:16]  # the pool's smaller two thirds (log-spaced sizes up to ~1e5 points), repeated
     tsample = (fiedler.fiedler_graph * len(tune))()
     for k, (gs, _) in enumerate(tune):
@@ -316,39 +317,37 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None)
     lat = np.full(nreq, np.nan)
     stats_st = np.zeros(nreq, np.int64)
     state = {"bad": 0, "t_last": 0.0, "stop": False, "err": None}
-    cond = threading.Condition()
+    lock = threading.Lock()
     t0 = 0.0
 
     def poller():
-        # polls every outstanding ticket without waiting, in submission order,
-        # and takes whichever have finished (a server answers requests as they
-        # complete, not in arrival order)
-        pending = []
+        # fiedler_poll_any lists tickets as they finish (in any order: a server
+        # answers requests as they complete), then each is collected
+        index = {}
         seen = 0
+        early = []
         done = 0
         while done < nreq and not state["stop"]:
-            with cond:
-                if seen == len(tickets) and not pending:
-                    cond.wait(timeout=1.0)
-                new = tickets[seen:]
-            pending.extend(range(seen, seen + len(new)))
-            seen += len(new)
-            keep = []
-            for k in pending:
-                r = fiedler.fiedler_result()
-                st = fiedler.fiedler_poll(plan.h, tickets[k], 0, r)
-                if st == fiedler.FIEDLER_EAGAIN:
-                    keep.append(k)
+            ids = early + plan.finished(1024, 100)
+            now = time.perf_counter()
+            with lock:
+                for k in range(seen, len(tickets)):
+                    index[tickets[k]] = k
+                seen = len(tickets)
+            early = []
+            for t in ids:
+                k = index.pop(t, None)
+                if k is None:  # finished before the submitter recorded it
+                    early.append(t)
                     continue
-                now = time.perf_counter()
+                st = fiedler.fiedler_poll(plan.h, t, 0, fiedler.fiedler_result())
                 lat[k] = now - t0 - t_arr[k]
                 stats_st[k] = st
                 state["bad"] += st != fiedler.FIEDLER_OK
                 state["t_last"] = now
                 done += 1
-            if len(keep) == len(pending):
-                time.sleep(2e-4)
-            pending = keep
+            if early:
+                time.sleep(1e-4)
 
     try:
         # warm-up: one request of each pool graph, one at a time
@@ -363,21 +362,23 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None)
         th.start()
         t0 = time.perf_counter()
         retries = 0
+        sub_ms = []
         for i in range(nreq):
             now = time.perf_counter() - t0
             if t_arr[i] > now:
                 time.sleep(t_arr[i] - now)
             while True:
+                c0 = time.perf_counter()
                 st, t = fiedler.fiedler_batch_submit(plan.h, dgs[pick[i]][0])
+                sub_ms.append(1e3 * (time.perf_counter() - c0))
                 if st != fiedler.FIEDLER_EAGAIN:
                     break
                 retries += 1
                 time.sleep(2e-4)
             if st != fiedler.FIEDLER_OK:
                 raise fiedler.FiedlerError(st, "fiedler_batch_submit")
-            with cond:
+            with lock:
                 tickets.append(t)
-                cond.notify()
         t_sub = time.perf_counter() - t0
         th.join(timeout=600.0)
         if th.is_alive():
@@ -385,8 +386,9 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None)
         ss = plan.serving_stats()
     finally:
         state["stop"] = True
-        with cond:
-            cond.notify_all()
+        th_ = locals().get("th")
+        if th_ is not None:
+            th_.join(timeout=5.0)
         plan.close()
     wall = shard.reduce_max(state["t_last"] - t0, dist, dev)  # every rank serves its own stream
     nall = shard.reduce_sum(nreq, dist, dev)
@@ -395,7 +397,9 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None)
         "workload": f"Poisson {rate:g} req/s for {seconds:g} s; kNN mixture graphs, {len(pool)} sizes log-spaced "
                     f"{SERVE['nmin']:g}..{SERVE['nmax']:g} points (largest component kept), seed {seed}",
         "requests": nreq, "completed_ok": int(nreq - state["bad"]), "submit_span_s": t_sub,
-        "submit_retries": retries, "wall_s": wall, "solves_per_s": nall / wall,
+        "submit_retries": retries, "wall_s": wall,
+        "submit_call_ms": {"p50": float(np.percentile(sub_ms, 50)), "p99": float(np.percentile(sub_ms, 99)),
+                           "max": float(np.max(sub_ms))}, "solves_per_s": nall / wall,
         "p50_ms": 1e3 * float(np.nanpercentile(lat, 50)), "p99_ms": 1e3 * float(np.nanpercentile(lat, 99)),
         "latency": "scheduled arrival to result, client side (includes waiting for queue room)",
         "library_p50_ms": ss.p50_ms, "library_p99_ms": ss.p99_ms,

@@ -161,8 +161,10 @@ fiedler_status fiedler_solve_batch(fiedler_plan *plan, const fiedler_graph *grap
  * copies the graph (host or device) into plan-owned memory, queues it and
  * returns a ticket at once; it returns FIEDLER_EAGAIN without queueing when
  * the copies held by earlier tickets (until they are polled) would exceed
- * queue_budget_bytes, so the caller can wait for completions and submit again
- * (back-pressure).  A scheduler thread admits queued tickets while the device
+ * queue_budget_bytes, or when the device has no memory left for the copy
+ * while earlier tickets hold some, so the caller can wait for completions and
+ * submit again (back-pressure; ENOMEM only when no other ticket holds
+ * memory).  A scheduler thread admits queued tickets while the device
  * memory of the tickets in flight (state, hierarchy arena, scratch) stays
  * within hbm_budget_bytes, at most max_batch per round, and publishes them to
  * a persistent kernel whose resident blocks (one graph each, as in the batched
@@ -180,6 +182,13 @@ fiedler_status fiedler_batch_submit(fiedler_plan *plan, const fiedler_graph *gra
  * host or device per x_on_device).  A finished ticket is forgotten after a
  * successful poll. */
 fiedler_status fiedler_poll(fiedler_plan *plan, uint64_t ticket, int timeout_ms, fiedler_result *result);
+
+/* Lists up to `max` tickets that finished since the last call (*count of them
+ * written to tickets[]), waiting up to timeout_ms (0 = do not wait, < 0 = wait
+ * forever) for at least one; EAGAIN if none.  Each is then collected with
+ * fiedler_poll (timeout 0), in any order: a server answers requests as they
+ * complete instead of waiting on the oldest. */
+fiedler_status fiedler_poll_any(fiedler_plan *plan, uint64_t *tickets, int max, int timeout_ms, int *count);
 
 /* Cancels a queued ticket (ECANCELED on its next poll); a ticket already on
  * the GPU completes normally.  EINVAL for unknown tickets. */

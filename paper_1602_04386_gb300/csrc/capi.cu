@@ -122,6 +122,7 @@ struct fiedler_plan {
   // ticket inputs and outputs: a stream-ordered pool on a stream of their own,
   // so that submit and poll never wait for the device as a whole
   cudaStream_t io_stream = nullptr;
+  cudaStream_t sub_stream = nullptr;  // fiedler_batch_submit's copies (waits only for its own)
   cudaMemPool_t pool = nullptr;
   // serving form: a persistent kernel fed through a ring in device memory
   fz::ServeRing *d_ring = nullptr;
@@ -130,6 +131,7 @@ struct fiedler_plan {
   unsigned long long *h_pub = nullptr;  // pinned staging: item pointers of a round, then the tail
   unsigned long long published = 0;
   static constexpr unsigned long long kIdleNs = 20000000ull;  // a serving block idle this long leaves
+  static constexpr int kReserveSms = 2;  // SMs whose block slots serving launches leave free
   struct ServeLaunch {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
@@ -148,6 +150,7 @@ struct fiedler_plan {
   std::mutex q_mu;
   std::condition_variable q_cv;
   std::deque<uint64_t> queue;
+  std::deque<uint64_t> finished;  // tickets done since they were last listed by fiedler_poll_any
   std::unordered_map<uint64_t, Ticket *> tickets;
   uint64_t next_ticket = 1;
   std::thread worker;
@@ -713,6 +716,20 @@ void ticket_result(const State *h, Ticket *t) {
   t->st = out;
 }
 
+// Marks a ticket finished (q_mu held) and lists it for fiedler_poll_any.  Ids
+// of tickets already collected by fiedler_poll are dropped from the list when
+// it outgrows the live tickets, so a caller that never lists stays bounded.
+void mark_done(fiedler_plan *p, Ticket *t) {
+  t->done = true;
+  p->finished.push_back(t->id);
+  if (p->finished.size() > 2 * p->tickets.size() + 1024) {
+    std::deque<uint64_t> keep;
+    for (uint64_t id : p->finished)
+      if (p->tickets.count(id)) keep.push_back(id);
+    p->finished.swap(keep);
+  }
+}
+
 void worker_main(fiedler_plan *p) {
   cudaSetDevice(p->device);
   const int type = p->opt.precision == FIEDLER_FP64 ? 0 : 1;
@@ -767,7 +784,7 @@ void worker_main(fiedler_plan *p) {
           if (ok)
             for (int ph = 0; ph < fz::PH_COUNT; ph++) p->block_seconds += h->phase_ns[1][ph] * 1e-9;
           if (ok && (h->status == fz::ST_ARENA || h->status == fz::ST_SCRATCH)) t->st = FIEDLER_ENOMEM;
-          t->done = true;
+          mark_done(p, t);
           t->running = false;
           p->n_completed++;
           p->latencies_ms.push_back(std::chrono::duration<float, std::milli>(now - t->t_submit).count());
@@ -790,7 +807,7 @@ void worker_main(fiedler_plan *p) {
         if (t->canceled) {
           p->queue.pop_front();
           t->st = FIEDLER_ECANCELED;
-          t->done = true;
+          mark_done(p, t);
           p->q_cv.notify_all();
           continue;
         }
@@ -820,7 +837,7 @@ void worker_main(fiedler_plan *p) {
           std::lock_guard<std::mutex> lk(p->q_mu);
           p->inflight_bytes -= t->footprint;
           t->st = FIEDLER_ENOMEM;
-          t->done = true;
+          mark_done(p, t);
           t->running = false;
           p->q_cv.notify_all();
           continue;
@@ -856,8 +873,11 @@ void worker_main(fiedler_plan *p) {
     }
     // 3. blocks for the published work: every unfinished ticket needs one;
     // blocks that find nothing to do leave after a short wait, so the alive
-    // count is read from their exit flags and topped up with a new launch
-    // (up to the blocks that fit on the device) when it falls short
+    // count is read from their exit flags and topped up with a new launch of
+    // the blocks still missing.  Launching only those, and never into the
+    // block slots of the last kReserveSms SMs, leaves room for other work on
+    // the device: a device-to-device copy (fiedler_batch_submit's) or another
+    // kernel would otherwise wait for resident serving blocks to leave.
     if (!p->live.empty()) {
       int alive = 0, freei = -1;
       unsigned long long oldest = p->block_next;
@@ -879,7 +899,8 @@ void worker_main(fiedler_plan *p) {
       int unfinished = 0;
       for (Ticket *t : p->live) unfinished += vd->done[t->k % fz::kRing] != t->k + 1ull;
       const int var = p->batch_var;
-      const int room = p->serve_slots[type][var] - alive;
+      const int slots = p->serve_slots[type][var], per_sm = slots / p->sms;
+      const int room = std::max(per_sm, slots - per_sm * fiedler_plan::kReserveSms) - alive;
       p->live_sum += (double)unfinished;
       p->alive_sum += (double)alive;
       p->live_rounds++;
@@ -898,9 +919,8 @@ void worker_main(fiedler_plan *p) {
           }
         }
         if (freei >= 0) {
-          // fill the device: blocks with nothing to do leave after kIdleNs
           fiedler_plan::ServeLaunch &L = p->serve[freei];
-          const int nb = std::min(room, fz::kServeSlots);
+          const int nb = std::min(want, fz::kServeSlots);
           unsigned long long base = p->block_next;
           void *args[] = {(void *)&p->d_ring, (void *)&p->done_dev, (void *)&base};
           if (cudaLaunchKernel(p->ks[type].serve_v[var], dim3(nb), dim3(fz::kBatchThreads[var]), args, 0, L.stream) ==
@@ -1042,6 +1062,7 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
   if (cudaMallocHost((void **)&p->h_stage, sizeof(State) * (size_t)p->stage_n) != cudaSuccess)
     return fail(FIEDLER_ENOMEM);
   if (cudaStreamCreateWithFlags(&p->io_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FIEDLER_ECUDA);
+  if (cudaStreamCreateWithFlags(&p->sub_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FIEDLER_ECUDA);
   {
     cudaMemPoolProps props = {};
     props.allocType = cudaMemAllocationTypePinned;
@@ -1096,7 +1117,7 @@ fiedler_status fiedler_batch_submit(fiedler_plan *p, const fiedler_graph *g, uin
     }
     p->queued_bytes += t->bytes;
   }
-  cudaError_t e = cudaMallocFromPoolAsync((void **)&t->buf, t->bytes, p->pool, p->io_stream);
+  cudaError_t e = cudaMallocFromPoolAsync((void **)&t->buf, t->bytes, p->pool, p->sub_stream);
   if (e == cudaSuccess) {
     t->rowptr = (int32_t *)t->buf;
     t->col = (int32_t *)(t->buf + rb);
@@ -1106,15 +1127,19 @@ fiedler_status fiedler_batch_submit(fiedler_plan *p, const fiedler_graph *g, uin
     t->buf = nullptr;
   }
   const cudaMemcpyKind kind = g->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  cudaStream_t io = p->io_stream;
+  cudaStream_t io = p->sub_stream;
   if (e == cudaSuccess) e = cudaMemcpyAsync(t->rowptr, g->rowptr, 4 * (size_t)(g->n + 1), kind, io);
   if (e == cudaSuccess && g->nnz > 0) e = cudaMemcpyAsync(t->col, g->col, 4 * (size_t)g->nnz, kind, io);
   if (e == cudaSuccess && g->nnz > 0) e = cudaMemcpyAsync(t->w, g->w, wsz * (size_t)g->nnz, kind, io);
   if (e == cudaSuccess) e = cudaStreamSynchronize(io);  // the copies only: the input may be freed on return
   if (e != cudaSuccess) {
     std::lock_guard<std::mutex> lk(p->q_mu);
+    // the pool is full while other tickets hold memory: that frees up as they
+    // complete and are polled, so the caller retries (back-pressure)
+    const bool busy = e == cudaErrorMemoryAllocation && (p->queued_bytes > t->bytes || p->inflight_bytes > 0);
+    if (busy) (void)cudaGetLastError();
     free_ticket(p, t);
-    return map_cuda(e);
+    return busy ? FIEDLER_EAGAIN : map_cuda(e);
   }
   t->footprint = item_footprint(g->n, g->nnz, p->opt.precision == FIEDLER_FP64 ? 8 : 4, g->w_dtype == FIEDLER_W_F64);
   t->t_submit = std::chrono::steady_clock::now();
@@ -1283,6 +1308,24 @@ fiedler_status fiedler_poll(fiedler_plan *p, uint64_t ticket, int timeout_ms, fi
   return st;
 }
 
+fiedler_status fiedler_poll_any(fiedler_plan *p, uint64_t *tickets, int max, int timeout_ms, int *count) {
+  if (!p || !tickets || max < 1 || !count) return FIEDLER_EINVAL;
+  std::unique_lock<std::mutex> lk(p->q_mu);
+  auto ready = [&] { return !p->finished.empty(); };
+  if (!ready()) {
+    if (timeout_ms < 0) p->q_cv.wait(lk, ready);
+    else if (timeout_ms > 0) p->q_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+  }
+  int k = 0;
+  while (k < max && !p->finished.empty()) {
+    const uint64_t id = p->finished.front();
+    p->finished.pop_front();
+    if (p->tickets.count(id)) tickets[k++] = id;  // still held (not polled yet)
+  }
+  *count = k;
+  return k > 0 ? FIEDLER_OK : FIEDLER_EAGAIN;
+}
+
 fiedler_status fiedler_cancel(fiedler_plan *p, uint64_t ticket) {
   if (!p) return FIEDLER_EINVAL;
   std::lock_guard<std::mutex> lk(p->q_mu);
@@ -1304,6 +1347,7 @@ void fiedler_plan_destroy(fiedler_plan *p) {
   for (auto &kv : p->tickets) free_ticket(p, kv.second);
   p->tickets.clear();
   if (p->io_stream) cudaStreamSynchronize(p->io_stream);
+  if (p->sub_stream) cudaStreamSynchronize(p->sub_stream);
   std::vector<BatchCtx *> ctxs{&p->bsync};
   for (BatchCtx *c : ctxs) {
     if (c->stream) cudaStreamSynchronize(c->stream);
@@ -1335,6 +1379,7 @@ void fiedler_plan_destroy(fiedler_plan *p) {
   if (p->h_pub) cudaFreeHost(p->h_pub);
   if (p->h_stage) cudaFreeHost(p->h_stage);
   if (p->io_stream) cudaStreamDestroy(p->io_stream);
+  if (p->sub_stream) cudaStreamDestroy(p->sub_stream);
   if (p->pool) cudaMemPoolDestroy(p->pool);
   delete p;
 }

@@ -44,7 +44,7 @@ SYMBOLS = (
     "fiedler_poll", "fiedler_cancel", "fiedler_plan_destroy", "fiedler_status_str",
     "fiedler_plan_num_levels", "fiedler_plan_level_info", "fiedler_plan_copy_level",
     "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc",
-    "fiedler_solve_batch", "fiedler_plan_serving_stats", "fiedler_plan_autotune",
+    "fiedler_solve_batch", "fiedler_plan_serving_stats", "fiedler_plan_autotune", "fiedler_poll_any",
 )
 
 
@@ -198,10 +198,11 @@ def load():
         L.fiedler_solve_batch.argtypes = [vp, C.POINTER(fiedler_graph), C.c_int, C.POINTER(fiedler_result)]
         L.fiedler_plan_serving_stats.argtypes = [vp, C.POINTER(fiedler_serving_stats)]
         L.fiedler_plan_autotune.argtypes = [vp, C.POINTER(fiedler_graph), C.c_int, C.POINTER(fiedler_tuning)]
+        L.fiedler_poll_any.argtypes = [vp, C.POINTER(C.c_uint64), C.c_int, C.c_int, C.POINTER(C.c_int)]
         for f in ("fiedler_plan_create", "fiedler_solve", "fiedler_batch_submit", "fiedler_poll", "fiedler_cancel",
                   "fiedler_plan_num_levels", "fiedler_plan_level_info", "fiedler_plan_copy_level",
                   "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc",
-                  "fiedler_solve_batch", "fiedler_plan_serving_stats", "fiedler_plan_autotune"):
+                  "fiedler_solve_batch", "fiedler_plan_serving_stats", "fiedler_plan_autotune", "fiedler_poll_any"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -232,6 +233,14 @@ def fiedler_batch_submit(plan, graph: fiedler_graph):
 
 def fiedler_poll(plan, ticket: int, timeout_ms: int, result: fiedler_result) -> int:
     return load().fiedler_poll(plan, ticket, timeout_ms, C.byref(result))
+
+
+def fiedler_poll_any(plan, max_count: int, timeout_ms: int):
+    """(status, [ticket ids]) of tickets finished since the last call."""
+    buf = (C.c_uint64 * max_count)()
+    cnt = C.c_int(0)
+    st = load().fiedler_poll_any(plan, buf, max_count, timeout_ms, C.byref(cnt))
+    return st, [buf[i] for i in range(cnt.value)]
 
 
 def fiedler_cancel(plan, ticket: int) -> int:
@@ -453,6 +462,13 @@ class Plan:
             r.x = x.ctypes.data
         st = fiedler_poll(self.h, ticket, timeout_ms, r)
         return st, Result(r, x)
+
+    def finished(self, max_count=256, timeout_ms=-1):
+        """Ids of tickets that finished since the last call (empty on timeout)."""
+        st, ids = fiedler_poll_any(self.h, max_count, timeout_ms)
+        if st not in (FIEDLER_OK, FIEDLER_EAGAIN):
+            raise FiedlerError(st, "fiedler_poll_any")
+        return ids
 
     def cancel(self, ticket) -> int:
         return fiedler_cancel(self.h, ticket)

@@ -178,3 +178,31 @@ def test_autotune_picks_a_block_size():
     with fiedler.Plan(batch_threads=256) as q:
         st, _ = fiedler.fiedler_plan_autotune(q.h, (fiedler.fiedler_graph * 1)())
         assert st == fiedler.FIEDLER_EINVAL  # a fixed block size is not tuned
+
+
+def test_poll_any_lists_each_finished_ticket_once():
+    """fiedler_poll_any lists every ticket once, as it finishes; collecting
+    them in that order gives the same results as alone; an empty list times
+    out (EAGAIN)."""
+    gs = mixed_grids(10, seed=21)
+    want = [alone(g, fiedler.FIEDLER_FP32_FP64RED) for g in gs]
+    with fiedler.Plan(max_batch=3) as p:
+        st, ids = fiedler.fiedler_poll_any(p.h, 4, 0)
+        assert st == fiedler.FIEDLER_EAGAIN and ids == []
+        tickets = [p.submit(g) for g in gs]
+        index = {t: i for i, t in enumerate(tickets)}
+        seen = []
+        deadline = time.time() + 120
+        while len(seen) < len(gs) and time.time() < deadline:
+            for t in p.finished(4, 1000):
+                i = index[t]
+                st, r = p.poll(t, 0, n=gs[i].n)
+                assert st == fiedler.FIEDLER_OK
+                assert r.lambda2 == want[i].lambda2 and np.array_equal(r.x, want[i].x)
+                seen.append(t)
+        assert sorted(seen) == sorted(tickets)
+        assert p.finished(4, 50) == []
+        # a ticket collected by fiedler_poll before it is listed is not listed
+        t = p.submit(gs[0])
+        assert p.poll(t, -1)[0] == fiedler.FIEDLER_OK
+        assert p.finished(4, 50) == []
