@@ -69,8 +69,10 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB_PATH)
+            # ORACLE_LIB names another build of fiedler_oracle.c (the mutation
+            # tests load copies with planted mistakes that way)
+            path = os.environ.get("ORACLE_LIB") or build()
+            L = C.CDLL(path)
             ip, dp, lp = C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_longlong)
             L.oracle_run_create.restype = C.c_void_p
             L.oracle_run_destroy.argtypes = [C.c_void_p]

@@ -203,6 +203,23 @@ def test_galerkin_matches_literal_product(gi):
     assert np.isclose(cw.sum(), cross, rtol=1e-13)
 
 
+@pytest.mark.parametrize("make,levels", [
+    (lambda: inputs.path(25), 1),     # n = 25 is not coarsened (Alg. 3: while n > 25)
+    (lambda: inputs.path(26), 2),     # n = 26 is, once
+    (lambda: inputs.random_connected(45, 4.0, seed=2), None),
+    (lambda: inputs.grid(7, 6, "uniform", seed=4), None),
+])
+def test_coarsening_stops_at_25_vertices(make, levels):
+    """Alg. 3 coarsens while a level has more than 25 vertices: the coarsest
+    level has at most 25 and every other level more than 25."""
+    g = make()
+    lv = oracle.build_hierarchy(g).levels
+    assert lv[-1].n <= 25
+    assert all(L.n > 25 for L in lv[:-1])
+    if levels is not None:
+        assert len(lv) == levels
+
+
 def test_hierarchy_invariants_and_stop_rule():
     g = inputs.grid(40, 30, "uniform", seed=9)
     r = oracle.build_hierarchy(g)
@@ -272,6 +289,35 @@ def test_gs_converges_to_linear_solve(colored):
     x = oracle.gauss_seidel(g.rowptr, g.col, g.w, d, b, np.zeros(g.n), 400, order)
     xs = np.linalg.solve(A, b)
     assert np.abs(x - xs).max() < 1e-11 * np.abs(xs).max()
+
+
+def test_smoothing_sweeps_colour_classes_in_order():
+    """With colour-class order, a level's sweep visits the classes in
+    ascending colour.  No two vertices of a class are adjacent, so the order
+    inside a class cannot change a single bit; the level's smoothed vector must
+    equal Alg. 2 (pinned above) run with every class shuffled, and differ from a
+    lexicographic sweep."""
+    g = inputs.grid(12, 10, "uniform", seed=3)
+    r = oracle.solve(g, gs_sweeps=1, forced_pi=[0] * 64)  # no power iteration: the sweep alone
+    assert r.status == 0
+    lv = r.levels
+    rng = np.random.default_rng(0)
+    differs = False
+    for j in range(len(lv) - 1):
+        F, Cl = lv[j], lv[j + 1]
+        x0 = Cl.x[F.agg].copy()                 # prolongation, then deflation and normalisation
+        x0 -= x0.mean()
+        x0 /= np.linalg.norm(x0)
+        order = np.concatenate([rng.permutation(np.flatnonzero(F.color == k)) for k in range(F.ncolors)])
+        x1 = oracle.gauss_seidel(F.rowptr, F.col, F.w, F.d, None, x0, 1, order)
+        x1 -= x1.mean()
+        x1 /= np.linalg.norm(x1)
+        assert np.abs(x1 - F.x).max() < 1e-12, j
+        xl = oracle.gauss_seidel(F.rowptr, F.col, F.w, F.d, None, x0, 1)
+        xl -= xl.mean()
+        xl /= np.linalg.norm(xl)
+        differs |= np.abs(xl - F.x).max() > 1e-6
+    assert differs
 
 
 # --------------------------------------------------------------------------
