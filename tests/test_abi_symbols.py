@@ -41,6 +41,19 @@ def test_calls_that_need_no_gpu(lib):
     assert fiedler.fiedler_plan_num_levels(None) == 0
     st, _ = fiedler.fiedler_plan_level_info(None, 0)
     assert st == fiedler.FIEDLER_EINVAL
+    st, ids = fiedler.fiedler_poll_any(None, 4, 0)
+    assert st == fiedler.FIEDLER_EINVAL and ids == []
+
+
+def test_plan_fails_loudly_without_a_gpu(lib):
+    """No CPU fallback: on a machine without a usable GPU, creating a plan
+    reports a CUDA error and the binding raises."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(fiedler.FiedlerError) as e:
+        fiedler.Plan()
+    assert e.value.status == fiedler.FIEDLER_ECUDA
 
 
 def _offsets(struct):
