@@ -171,9 +171,11 @@ fiedler_status fiedler_solve_batch(fiedler_plan *plan, const fiedler_graph *grap
  * form, batch_threads per block) take them in order and finish each one
  * independently: a ticket admitted while others are on the GPU starts as soon
  * as a block is free, and a finished ticket returns its memory at once.
- * Thread-safe against fiedler_poll / fiedler_cancel.  While tickets are in
- * flight the serving kernel may occupy every SM, so a plan's fiedler_solve
- * should not run at the same time on the same device. */
+ * Thread-safe against fiedler_poll / fiedler_cancel.  Serving launches add
+ * only the blocks that unfinished tickets lack and leave the block slots of
+ * two SMs free, so copies and small kernels of other streams keep running;
+ * a plan's fiedler_solve (a cooperative launch over every SM) should still
+ * not run at the same time on the same device. */
 fiedler_status fiedler_batch_submit(fiedler_plan *plan, const fiedler_graph *graph, uint64_t *ticket);
 
 /* Waits up to timeout_ms (0 = do not wait, < 0 = wait forever) for a ticket.
