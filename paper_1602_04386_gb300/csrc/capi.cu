@@ -669,9 +669,9 @@ void free_ticket(fiedler_plan *p, Ticket *t) {
 // tickets in order and flag each as soon as it is done; the scheduler reads
 // the flags, copies the finished state back and completes the ticket, which
 // returns its memory to the budget at once.  A long solve therefore holds one
-// block, not a launch.  The kernel's blocks leave after an idle spell; the
-// scheduler launches it again whenever published work is waiting and no block
-// is left.
+// block, not a launch.  The kernel's blocks leave after an idle spell; when
+// unfinished tickets outnumber the blocks still alive, the scheduler launches
+// the missing ones (never into the last kReserveSms SMs' block slots).
 
 // fills the device-side state header of a ticket (host copy in *h)
 void fill_ticket_state(fiedler_plan *p, Ticket *t, State *h, int type, size_t arena_b, size_t scratch_b) {
