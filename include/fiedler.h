@@ -49,7 +49,7 @@ typedef enum {
   FIEDLER_ECUDA = -6,            /* a CUDA runtime call failed */
   FIEDLER_ECANCELED = -7,        /* the ticket was cancelled */
   FIEDLER_EDEGENERATE = -8,      /* an iterate vanished after deflation (cannot be normalised) */
-  FIEDLER_ENOTSUP = -9           /* a size limit of this build was exceeded */
+  FIEDLER_ENOTSUP = -9           /* a compiled-in size limit was exceeded */
 } fiedler_status;
 
 /* fiedler_options.precision */
