@@ -668,13 +668,28 @@ def main():
                                     "sample": f"{nrep} whole solves of {workload_name()} (single-threaded C)",
                                     "lambda2": ro.lam}
     plan.close()
+
+    def extra_leg(name, fn):
+        # one process: a failing extra leg is reported in the line, under its
+        # own key, and the main measurement above is still printed (several
+        # ranks cannot skip a leg alone: they share its collectives)
+        if dist is not None:
+            return fn()
+        try:
+            return fn()
+        except Exception as e:  # noqa: BLE001 - reported, not hidden
+            print(f"bench: {name} leg failed: {e!r}", file=sys.stderr)
+            return {"error": f"{type(e).__name__}: {e}"}
+
     if batch_graphs is not None:
-        line["batched"] = batched_leg(batch_graphs, stream, dev, dist=dist)
-        line["gpu_launches_batched_per_batch"] = line["batched"]["gpu_launches_per_batch"]
+        line["batched"] = extra_leg("batched", lambda: batched_leg(batch_graphs, stream, dev, dist=dist))
+        if "gpu_launches_per_batch" in line["batched"]:
+            line["gpu_launches_batched_per_batch"] = line["batched"]["gpu_launches_per_batch"]
         del batch_graphs
     if serve_pool is not None:
-        line["serving"] = serving_leg(serve_pool, stream, dev, args.serve_rate, args.serve_seconds,
-                                      seed=SERVE["seed"] + 7919 * rank, dist=dist)
+        line["serving"] = extra_leg("serving", lambda: serving_leg(
+            serve_pool, stream, dev, args.serve_rate, args.serve_seconds, seed=SERVE["seed"] + 7919 * rank,
+            dist=dist))
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
