@@ -1004,7 +1004,6 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
   fiedler_plan *p = new (std::nothrow) fiedler_plan();
   if (!p) return FIEDLER_ENOMEM;
   p->opt = o;
-  fiedler_status st = FIEDLER_OK;
   auto fail = [&](fiedler_status s) {
     fiedler_plan_destroy(p);
     return s;
@@ -1082,7 +1081,6 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
     if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return fail(FIEDLER_ECUDA);
   p->worker = std::thread(worker_main, p);
   *out = p;
-  (void)st;
   return FIEDLER_OK;
 }
 
