@@ -56,3 +56,29 @@ def test_batch_mix_alternates_families():
     for g in gs:
         check_csr(g)
         assert connected(g)
+
+
+def test_serving_pool_sizes_and_seeds():
+    """The serving pool: point counts log-spaced between nmin and nmax, graph i
+    drawn with seed + i (the same graph as knn_mixture with that seed), each
+    one connected (its largest component kept) and symmetric."""
+    pool = inputs.serving_pool(5, 200, 3200, seed=77)
+    assert len(pool) == 5
+    want = np.exp(np.linspace(np.log(200), np.log(3200), 5)).round().astype(np.int64)
+    assert list(want) == [200, 400, 800, 1600, 3200]
+    for i, (g, npts) in enumerate(zip(pool, want)):
+        assert npts // 8 <= g.n <= npts  # the largest component: at least one of the 8 clusters
+        ref = inputs.knn_mixture(int(npts), seed=77 + i)
+        assert g.n == ref.n and np.array_equal(g.col, ref.col) and np.array_equal(g.w, ref.w)
+        W = g.dense()
+        assert np.array_equal(W, W.T) and (W.diagonal() == 0).all()
+        seen = np.zeros(g.n, bool)  # connected: a traversal from vertex 0 reaches all
+        stack = [0]
+        seen[0] = True
+        while stack:
+            v = stack.pop()
+            for u in g.col[g.rowptr[v]:g.rowptr[v + 1]]:
+                if not seen[u]:
+                    seen[u] = True
+                    stack.append(int(u))
+        assert seen.all()
