@@ -95,3 +95,39 @@ int main(void){
                      C.sizeof(fiedler.fiedler_profile)]
     assert offs == [fiedler.fiedler_options.seed.offset, fiedler.fiedler_result.x.offset,
                     fiedler.fiedler_result.bad_index.offset, fiedler.fiedler_profile.phase_bytes.offset]
+
+
+def test_c_program_links_and_runs(lib):
+    """A plain C program includes the header, links the library and calls the
+    entry points that need no GPU; without a usable GPU, plan creation returns
+    a CUDA error and a NULL plan."""
+    import subprocess
+    import tempfile
+    import torch
+    src = r'''
+#include <stdio.h>
+#include "fiedler.h"
+int main(void) {
+  fiedler_options o;
+  fiedler_options_default(&o);
+  if (o.coarse_max_n != 25) return 2;
+  printf("%s\n", fiedler_status_str(FIEDLER_EDISCONNECTED));
+  fiedler_plan *p = (fiedler_plan *)1;
+  fiedler_status st = fiedler_plan_create(&o, NULL, &p);
+  printf("%d %d\n", (int)st, p == NULL);
+  if (st == FIEDLER_OK) fiedler_plan_destroy(p);
+  return 0;
+}
+'''
+    libdir = os.path.dirname(build.LIB)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe, "-L", libdir, "-lfiedler",
+                               "-Wl,-rpath," + libdir])
+        out = subprocess.check_output([exe], timeout=120).decode().split("\n")
+    assert out[0] == "graph is not connected"
+    st, null = (int(v) for v in out[1].split())
+    if not torch.cuda.is_available():
+        assert st == fiedler.FIEDLER_ECUDA and null == 1
