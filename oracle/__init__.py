@@ -57,12 +57,18 @@ class Opts(C.Structure):
         ("guard", C.c_double),
         ("seed", C.c_uint64),
         ("coarsest_dense", C.c_int),
+        ("refine", C.c_int),
+        ("refine_max_iters", C.c_int),
+        ("refine_tol", C.c_double),
+        ("lanczos_basis", C.c_int),
+        ("refine_forced", C.c_int),
     ]
 
 
 HEC_HANDSHAKE, HEC_GREEDY, HEC_PAPER = 0, 1, 2
 TIE_HASHED, TIE_INDEX = 0, 1
 GS_LEX, GS_COLORED = 0, 1
+REFINE_NONE, REFINE_LOBPCG, REFINE_LANCZOS = 0, 1, 2
 
 
 def lib():
@@ -153,7 +159,7 @@ class Run:
         return lib().oracle_run_num_levels(self._h)
 
     def level(self, l) -> Level:
-        info = np.zeros(10, dtype=np.int64)
+        info = np.zeros(12, dtype=np.int64)
         dinfo = np.zeros(2, dtype=np.float64)
         lib().oracle_run_level_info(self._h, l, info.ctypes.data_as(C.POINTER(C.c_longlong)), _dp(dinfo))
         n, nnz = int(info[0]), int(info[1])
@@ -169,6 +175,7 @@ class Run:
                                     _ip(color), _dp(x))
         return Level(n=n, nnz=nnz, nc=int(info[2]), ncolors=int(info[3]), match_rounds=int(info[4]),
                      gs_sweeps=int(info[5]), pi_iters=int(info[6]), color_rounds=int(info[9]),
+                     refine_iters=int(info[10]), capped=int(info[11]),
                      sigma=float(dinfo[0]), last_cos=float(dinfo[1]), rowptr=rowptr, col=col[:nnz], w=w[:nnz],
                      d=d, agg=agg, mate=mate, color=color, x=x)
 
@@ -200,6 +207,14 @@ class Run:
     @property
     def pi_iters(self):
         return [self.level(l).pi_iters for l in range(self.num_levels)]
+
+    @property
+    def refine_iters(self):
+        return self.level(0).refine_iters if self.num_levels else 0
+
+    @property
+    def capped(self):
+        return any(self.level(l).capped for l in range(self.num_levels))
 
 
 def build_hierarchy(g, **kw) -> Run:

@@ -58,6 +58,23 @@
  *       Jones-Plassmann rounds with that priority.
  *   R8  random start: x_i = uniform draw i of the splitmix64 stream of `seed`.
  *   R9  output sign: the entry of largest |x_i| (lowest index on ties) is >= 0.
+ *   R11 randperm of Alg. 1 (hec_mode 2): the visiting order of level l is the
+ *       ascending order of the keys splitmix64(seed + l, v), ties by v (a
+ *       uniformly random order when the keys are distinct).
+ *   R12 Krylov refinement of the finest level (refine 1 or 2; Sec. 4 names a
+ *       Lanczos smoother as future work): with it on, the finest level skips
+ *       its power iteration and, after its Gauss-Seidel sweeps, runs
+ *       (1) LOBPCG (Knyazev 2001), one vector, on 1-perp with preconditioner
+ *           D^-1: w = D^-1 (L x - theta x) with its mean removed, Rayleigh-Ritz
+ *           on span{x, w, p} (columns scaled to unit norm; w, then p, dropped
+ *           when its Cholesky pivot of the scaled Gram matrix is <= 1e-10),
+ *           x and p = the w, p part of the Ritz vector, both normalised;
+ *       (2) Lanczos with full reorthogonalisation (classical Gram-Schmidt,
+ *           twice) on 1-perp, restarted from the smallest Ritz vector every
+ *           lanczos_basis steps;
+ *       until ||L x - theta x|| <= refine_tol * theta * ||x|| (LOBPCG: tested
+ *       before every step; Lanczos: the Ritz estimate beta_m |s_m| at the end
+ *       of a cycle), or refine_max_iters matvecs.
  */
 #include <math.h>
 #include <stdint.h>
@@ -117,6 +134,11 @@ typedef struct {
   double guard;              /* annihilation guard, 2^-20 */
   uint64_t seed;             /* random start on the coarsest level */
   int coarsest_dense;        /* 1 = coarsest eigenvector by dense Jacobi */
+  int refine;                /* 0 none (paper), 1 LOBPCG, 2 Lanczos on the finest level (R12) */
+  int refine_max_iters;      /* matvec cap of the refinement */
+  double refine_tol;         /* stop: ||L x - theta x|| <= refine_tol * theta * ||x|| */
+  int lanczos_basis;         /* Lanczos steps per restart cycle */
+  int refine_forced;         /* >= 0: run exactly this many matvecs (replay); -1: stop rule */
 } oracle_opts;
 
 typedef struct {
@@ -139,6 +161,8 @@ typedef struct {
   int gs_sweeps_done;
   int pi_iters;
   double last_cos;
+  int refine_iters;
+  int capped; /* a power-iteration or refinement cap was reached */
   double *x; /* level result after smoothing */
 } orc_level;
 
@@ -198,6 +222,11 @@ void oracle_default_opts(oracle_opts *o) {
   o->guard = 9.5367431640625e-07; /* 2^-20 */
   o->seed = 20160214ULL;
   o->coarsest_dense = 0;
+  o->refine = 0;
+  o->refine_max_iters = 5000;
+  o->refine_tol = 1e-4;
+  o->lanczos_basis = 24;
+  o->refine_forced = -1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -388,8 +417,19 @@ static int aggregate_from_matching(const orc_lap *L, const int *mate, int tie_ru
 /* Alg. 1 as printed: random order p; for each unaggregated p(i), m = argmin of
  * column p(i) of L (the heaviest neighbour, lowest index on ties); pair with m
  * if m is unaggregated, else join m's aggregate.  A vertex without neighbours
- * becomes a singleton. `perm` may be given; otherwise Fisher-Yates on the
- * splitmix64 stream of `seed`. */
+ * becomes a singleton. `perm` may be given; otherwise the vertices sorted by
+ * the keys splitmix64(seed, v), ties by v (reading R11). */
+typedef struct {
+  uint64_t key;
+  int v;
+} orc_keyv;
+
+static int keyv_cmp(const void *p, const void *q) {
+  const orc_keyv *a = (const orc_keyv *)p, *b = (const orc_keyv *)q;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  return a->v < b->v ? -1 : (a->v > b->v);
+}
+
 static int hec_paper(const orc_lap *L, uint64_t seed, const int *perm_in, int *agg) {
   int n = L->n;
   int *p = (int *)malloc(sizeof(int) * (size_t)n);
@@ -398,11 +438,15 @@ static int hec_paper(const orc_lap *L, uint64_t seed, const int *perm_in, int *a
   if (perm_in) {
     memcpy(p, perm_in, sizeof(int) * (size_t)n);
   } else {
-    for (int i = 0; i < n; i++) p[i] = i;
-    for (int i = n - 1; i > 0; i--) {
-      int j = (int)(orc_uniform(seed, (uint64_t)(n - 1 - i)) * (double)(i + 1));
-      int t = p[i]; p[i] = p[j]; p[j] = t;
+    orc_keyv *kv = (orc_keyv *)malloc(sizeof(orc_keyv) * (size_t)n);
+    if (!kv) { free(p); free(q); return ORC_ENOMEM; }
+    for (int i = 0; i < n; i++) {
+      kv[i].key = oracle_splitmix64(seed, (uint64_t)i);
+      kv[i].v = i;
     }
+    qsort(kv, (size_t)n, sizeof(orc_keyv), keyv_cmp);
+    for (int i = 0; i < n; i++) p[i] = kv[i].v;
+    free(kv);
   }
   for (int i = 0; i < n; i++) q[i] = 0;
   int c = 0;
@@ -777,8 +821,216 @@ static int smooth_level(orc_level *lv, double *x, const oracle_opts *o, int kmax
     lv->last_cos = c;
     if (forced >= 0) continue;
     if (c > 1.0 - o->pi_cos_tol && (o->resid_tol <= 0.0 || r <= o->resid_tol * sigma)) break;
+    if (k == limit) lv->capped = 1;
   }
   free(old); free(y); free(tmp); free(order);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Krylov refinement of the finest level (reading R12). */
+
+/* Rayleigh-Ritz on the k <= 3 columns S[0..k) (unit-free): Gram matrix
+ * G = S^T S and projection H = S^T L S are formed from the columns and their
+ * L-products; the columns are scaled to unit norm; column 2 (p), then column 1
+ * (w), is dropped while its Cholesky pivot of the scaled Gram matrix is
+ * <= 1e-10; the reduced symmetric problem R^-1 Hs R^-T is solved by the dense
+ * Jacobi eigensolver.  On return c[0..3) holds the coefficients of the smallest
+ * Ritz vector in the original columns (0 for dropped ones); the return value
+ * is the number of columns kept (1: no step possible). */
+static int rayleigh_ritz(int n, double *const *Sv, double *const *LS, int k, double *c) {
+  double G[3][3], H[3][3];
+  for (int a = 0; a < k; a++)
+    for (int b = 0; b < k; b++) {
+      G[a][b] = vdot(n, Sv[a], Sv[b]);
+      H[a][b] = vdot(n, Sv[a], LS[b]);
+    }
+  int act[3], m;
+  double D[3], R[3][3];
+  int keep[3] = {1, k > 1, k > 2};
+  for (;;) {
+    m = 0;
+    for (int a = 0; a < k; a++)
+      if (keep[a]) act[m++] = a;
+    for (int i = 0; i < m; i++) D[i] = 1.0 / sqrt(G[act[i]][act[i]]);
+    int bad = -1;
+    for (int i = 0; i < m && bad < 0; i++)
+      for (int j = 0; j <= i; j++) {
+        double sum = G[act[i]][act[j]] * D[i] * D[j];
+        for (int q = 0; q < j; q++) sum -= R[i][q] * R[j][q];
+        if (i == j) {
+          if (!(sum > 1e-10)) { bad = i; break; }
+          R[i][i] = sqrt(sum);
+        } else {
+          R[i][j] = sum / R[j][j];
+        }
+      }
+    if (bad < 0) break;
+    if (bad == 0) return 1;
+    keep[act[bad]] = 0;
+  }
+  c[0] = c[1] = c[2] = 0.0;
+  if (m == 1) return 1;
+  /* M = R^-1 Hs R^-T, Hs = D H D */
+  double Rinv[3][3], M[9], ev[3], V[9];
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < m; j++) {
+      double sum = (i == j) ? 1.0 : 0.0;
+      for (int q = 0; q < i; q++) sum -= R[i][q] * Rinv[q][j];
+      Rinv[i][j] = sum / R[i][i];
+    }
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < m; j++) {
+      double sum = 0.0;
+      for (int a = 0; a < m; a++)
+        for (int b = 0; b < m; b++)
+          sum += Rinv[i][a] * (H[act[a]][act[b]] * D[a] * D[b]) * Rinv[j][b];
+      M[i * m + j] = sum;
+    }
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < i; j++) M[i * m + j] = M[j * m + i] = 0.5 * (M[i * m + j] + M[j * m + i]);
+  oracle_jacobi_eig(m, M, ev, V, 100, 1e-16);
+  /* y = R^-T u for the smallest pair, then undo the column scaling */
+  for (int a = 0; a < m; a++) {
+    double y = 0.0;
+    for (int i = 0; i < m; i++) y += Rinv[i][a] * V[i * m + 0];
+    c[act[a]] = D[a] * y;
+  }
+  return m;
+}
+
+/* (1) LOBPCG with preconditioner D^-1 on 1-perp.  x: unit vector, orthogonal
+ * to 1, replaced by the refined vector.  forced >= 0 runs that many steps. */
+static int refine_lobpcg(orc_level *lv, double *x, const oracle_opts *o) {
+  const orc_lap *L = &lv->L;
+  int n = L->n;
+  double *lx = (double *)malloc(sizeof(double) * (size_t)n);
+  double *w = (double *)malloc(sizeof(double) * (size_t)n);
+  double *lw = (double *)malloc(sizeof(double) * (size_t)n);
+  double *p = (double *)calloc((size_t)n, sizeof(double));
+  double *lp = (double *)calloc((size_t)n, sizeof(double));
+  double *xn = (double *)malloc(sizeof(double) * (size_t)n);
+  if (!lx || !w || !lw || !p || !lp || !xn) {
+    free(lx); free(w); free(lw); free(p); free(lp); free(xn);
+    return ORC_ENOMEM;
+  }
+  int forced = o->refine_forced, pvalid = 0, k = 0;
+  lap_apply(L, x, lx);
+  double theta = vdot(n, x, lx) / vdot(n, x, x);
+  for (;;) {
+    double rr = 0.0;
+    for (int i = 0; i < n; i++) {
+      w[i] = lx[i] - theta * x[i]; /* residual r, then w = D^-1 r */
+      rr += w[i] * w[i];
+    }
+    if (forced < 0 && sqrt(rr) <= o->refine_tol * theta * sqrt(vdot(n, x, x))) break;
+    if (forced >= 0 && k >= forced) break;
+    if (forced < 0 && k >= o->refine_max_iters) { lv->capped = 1; break; }
+    for (int i = 0; i < n; i++) w[i] /= L->d[i];
+    double mw = vsum(n, w) / (double)n;
+    for (int i = 0; i < n; i++) w[i] -= mw;
+    lap_apply(L, w, lw);
+    k++;
+    double *Sv[3] = {x, w, p}, *LS[3] = {lx, lw, lp};
+    double c[3];
+    int kept = rayleigh_ritz(n, Sv, LS, pvalid ? 3 : 2, c);
+    if (kept == 1) break; /* no step left: x is final */
+    for (int i = 0; i < n; i++) {
+      xn[i] = c[0] * x[i] + c[1] * w[i] + c[2] * p[i];
+      p[i] = c[1] * w[i] + c[2] * p[i];
+    }
+    double pn = sqrt(vdot(n, p, p));
+    pvalid = pn > 0.0;
+    if (pvalid) {
+      for (int i = 0; i < n; i++) p[i] /= pn;
+      lap_apply(L, p, lp);
+    }
+    double s = deflate(n, xn);
+    for (int i = 0; i < n; i++) x[i] = xn[i] / s;
+    lap_apply(L, x, lx);
+    theta = vdot(n, x, lx) / vdot(n, x, x);
+  }
+  lv->refine_iters = k;
+  free(lx); free(w); free(lw); free(p); free(lp); free(xn);
+  return ORC_OK;
+}
+
+/* (2) Lanczos on 1-perp with full reorthogonalisation, restarted from the
+ * smallest Ritz vector every lanczos_basis steps (Golub & Van Loan, Sec. 10.1;
+ * explicit restart).  Convergence is tested at the end of each cycle with the
+ * Ritz estimate beta_m |s_m| (the residual of the Ritz pair in exact
+ * arithmetic). */
+static int refine_lanczos(orc_level *lv, double *x, const oracle_opts *o) {
+  const orc_lap *L = &lv->L;
+  int n = L->n, m = o->lanczos_basis;
+  if (m < 1) return ORC_EINVAL;
+  double *Q = (double *)malloc(sizeof(double) * (size_t)n * (size_t)(m + 1));
+  double *u = (double *)malloc(sizeof(double) * (size_t)n);
+  double *h = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+  double *al = (double *)malloc(sizeof(double) * (size_t)m);
+  double *be = (double *)malloc(sizeof(double) * (size_t)m);
+  double *T = (double *)malloc(sizeof(double) * (size_t)m * (size_t)m);
+  double *V = (double *)malloc(sizeof(double) * (size_t)m * (size_t)m);
+  double *ev = (double *)malloc(sizeof(double) * (size_t)m);
+  if (!Q || !u || !h || !al || !be || !T || !V || !ev) {
+    free(Q); free(u); free(h); free(al); free(be); free(T); free(V); free(ev);
+    return ORC_ENOMEM;
+  }
+  int forced = o->refine_forced, total = 0;
+  double s0 = deflate(n, x);
+  for (int i = 0; i < n; i++) x[i] /= s0;
+  for (;;) {
+    memcpy(Q, x, sizeof(double) * (size_t)n);
+    int kk = 0;
+    for (int j = 0; j < m; j++) {
+      if (forced >= 0 ? total >= forced : total >= o->refine_max_iters) break;
+      const double *q = Q + (size_t)j * n;
+      lap_apply(L, q, u);
+      total++;
+      double mu = vsum(n, u) / (double)n;
+      for (int i = 0; i < n; i++) u[i] -= mu;
+      al[j] = vdot(n, q, u);
+      for (int i = 0; i < n; i++) u[i] -= al[j] * q[i];
+      if (j > 0)
+        for (int i = 0; i < n; i++) u[i] -= be[j - 1] * Q[(size_t)(j - 1) * n + i];
+      for (int pass = 0; pass < 2; pass++) {
+        for (int t = 0; t <= j; t++) h[t] = vdot(n, Q + (size_t)t * n, u);
+        for (int t = 0; t <= j; t++)
+          for (int i = 0; i < n; i++) u[i] -= h[t] * Q[(size_t)t * n + i];
+      }
+      be[j] = sqrt(vdot(n, u, u));
+      kk = j + 1;
+      if (!(be[j] > 1e-12 * fabs(al[j]))) break; /* invariant subspace */
+      for (int i = 0; i < n; i++) Q[(size_t)(j + 1) * n + i] = u[i] / be[j];
+    }
+    if (kk == 0) { /* cap reached at a cycle boundary */
+      if (forced < 0) lv->capped = 1;
+      break;
+    }
+    for (int a = 0; a < kk * kk; a++) T[a] = 0.0;
+    for (int a = 0; a < kk; a++) {
+      T[a * kk + a] = al[a];
+      if (a + 1 < kk) T[a * kk + a + 1] = T[(a + 1) * kk + a] = be[a];
+    }
+    oracle_jacobi_eig(kk, T, ev, V, 100, 1e-16);
+    double theta = ev[0];
+    for (int i = 0; i < n; i++) {
+      double y = 0.0;
+      for (int t = 0; t < kk; t++) y += V[t * kk + 0] * Q[(size_t)t * n + i];
+      x[i] = y;
+    }
+    double s = deflate(n, x);
+    for (int i = 0; i < n; i++) x[i] /= s;
+    double est = be[kk - 1] * fabs(V[(kk - 1) * kk + 0]);
+    if (forced >= 0) {
+      if (total >= forced) break;
+      continue;
+    }
+    if (est <= o->refine_tol * theta) break;
+    if (total >= o->refine_max_iters) { lv->capped = 1; break; }
+  }
+  lv->refine_iters = total;
+  free(Q); free(u); free(h); free(al); free(be); free(T); free(V); free(ev);
   return ORC_OK;
 }
 
@@ -829,7 +1081,7 @@ static int build_hierarchy(oracle_run *r, const oracle_opts *o) {
     if (!agg) return ORC_ENOMEM;
     int nc;
     if (o->hec_mode == 2) {
-      nc = hec_paper(&lv->L, o->seed + (uint64_t)r->nlevels, NULL, agg);
+      nc = hec_paper(&lv->L, o->seed + (uint64_t)(r->nlevels - 1), NULL, agg);
     } else {
       lv->mate = (int *)malloc(sizeof(int) * (size_t)n);
       if (!lv->mate) { free(agg); return ORC_ENOMEM; }
@@ -899,7 +1151,8 @@ int oracle_solve(oracle_run *r, int n, long long nnz, const int *rowptr, const i
     double s = deflate(nJ, x);
     if (!(s > o->guard)) { free(x); r->status = ORC_EDEGENERATE; return ORC_EDEGENERATE; }
     vscale(nJ, x, s);
-    st = smooth_level(cl, x, o, o->pi_max_iters_coarsest, forced_pi ? forced_pi[J] : -1);
+    st = smooth_level(cl, x, o, (J == 0 && o->refine) ? 0 : o->pi_max_iters_coarsest,
+                      (J == 0 && o->refine) ? 0 : (forced_pi ? forced_pi[J] : -1));
     if (st != ORC_OK) { free(x); return st; }
   }
   cl->x = x;
@@ -914,9 +1167,16 @@ int oracle_solve(oracle_run *r, int n, long long nnz, const int *rowptr, const i
     double s = deflate(nf, xf);
     if (!(s > o->guard)) { free(xf); r->status = ORC_EDEGENERATE; return ORC_EDEGENERATE; }
     vscale(nf, xf, s);
-    st = smooth_level(lv, xf, o, o->pi_max_iters, forced_pi ? forced_pi[j] : -1);
+    st = smooth_level(lv, xf, o, (j == 0 && o->refine) ? 0 : o->pi_max_iters,
+                      (j == 0 && o->refine) ? 0 : (forced_pi ? forced_pi[j] : -1));
     if (st != ORC_OK) { free(xf); return st; }
     lv->x = xf;
+  }
+  /* finest-level Krylov refinement (reading R12) */
+  if (o->refine == 1 || o->refine == 2) {
+    orc_level *l0 = &r->lv[0];
+    st = (o->refine == 1) ? refine_lobpcg(l0, l0->x, o) : refine_lanczos(l0, l0->x, o);
+    if (st != ORC_OK) return st;
   }
   /* Rayleigh quotient on the finest level, residual, orthogonality, sign */
   orc_lap *L0 = &r->lv[0].L;
@@ -965,6 +1225,8 @@ void oracle_run_level_info(const oracle_run *r, int l, long long *info, double *
   info[7] = lv->agg != NULL;
   info[8] = lv->x != NULL;
   info[9] = lv->color_rounds;
+  info[10] = lv->refine_iters;
+  info[11] = lv->capped;
   dinfo[0] = lv->sigma;
   dinfo[1] = lv->last_cos;
 }

@@ -58,6 +58,23 @@ MUTANTS = [
     ("prolongation_wrong_index", "xf[i] = xc[lv->agg[i]];", "xf[i] = xc[i % r->lv[j + 1].L.n];"),
     ("stop_rule_looser", "if (c > 1.0 - o->pi_cos_tol &&", "if (c > 1.0 - 100.0 * o->pi_cos_tol &&"),
     ("sign_rule_reversed", "if (r->x[imax] < 0.0)", "if (r->x[imax] > 0.0)"),
+    # Alg. 1's random order (reading R11)
+    ("paper_order_descending", "if (a->key != b->key) return a->key < b->key ? -1 : 1;",
+     "if (a->key != b->key) return a->key < b->key ? 1 : -1;"),
+    ("paper_order_level_seed", "o->seed + (uint64_t)(r->nlevels - 1)", "o->seed + (uint64_t)r->nlevels"),
+    # finest-level Krylov refinement (reading R12)
+    ("lobpcg_preconditioner_inverted", "for (int i = 0; i < n; i++) w[i] /= L->d[i];",
+     "for (int i = 0; i < n; i++) w[i] *= L->d[i];"),
+    ("lobpcg_keeps_constant_in_w", "for (int i = 0; i < n; i++) w[i] -= mw;",
+     "for (int i = 0; i < n; i++) w[i] -= 0.0 * mw;"),
+    ("lobpcg_largest_ritz_vector", "for (int i = 0; i < m; i++) y += Rinv[i][a] * V[i * m + 0];",
+     "for (int i = 0; i < m; i++) y += Rinv[i][a] * V[i * m + (m - 1)];"),
+    ("lobpcg_stop_rule_absolute", "sqrt(rr) <= o->refine_tol * theta * sqrt(vdot(n, x, x))",
+     "sqrt(rr) <= o->refine_tol * sqrt(vdot(n, x, x))"),
+    ("lanczos_alpha_halved", "      al[j] = vdot(n, q, u);\n", "      al[j] = 0.5 * vdot(n, q, u);\n"),
+    ("lanczos_largest_ritz_vector", "y += V[t * kk + 0] * Q[(size_t)t * n + i];",
+     "y += V[t * kk + (kk - 1)] * Q[(size_t)t * n + i];"),
+    ("lanczos_estimate_wrong_entry", "fabs(V[(kk - 1) * kk + 0])", "fabs(V[0 * kk + 0])"),
     # truth references and generators used by the pins themselves
     ("jacobi_rotation_sign", "A[k * n + p] = c * akp - s * akq;", "A[k * n + p] = c * akp + s * akq;"),
     ("splitmix_constant", "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 27)) * 0x94D049BB133111EFULL;"),

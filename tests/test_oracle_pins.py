@@ -480,3 +480,135 @@ def test_star_graph():
     g = inputs.star(40)
     r = oracle.solve(g, **TIGHT)
     assert r.status == 0 and abs(r.lam - 1.0) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Alg. 1's random order (reading R11) and the finest-level Krylov refinement
+# (reading R12: Sec. 4's Krylov smoother)
+
+def test_paper_hec_order_is_sorted_splitmix_keys():
+    """Without an explicit order, hec_paper visits the vertices in ascending
+    order of splitmix64(seed, v) (ties by v): the same aggregates as the order
+    computed here from the published generator; the hierarchy's level l uses
+    seed + l."""
+    g = inputs.random_connected(120, 4.0, seed=5)
+    for seed in (3, 20160214):
+        keys = inputs.splitmix64(seed, np.arange(g.n))
+        perm = np.lexsort((np.arange(g.n), keys))
+        a1, n1 = oracle.hec_paper(g, seed=seed)
+        a2, n2 = oracle.hec_paper(g, perm=perm)
+        assert n1 == n2 and np.array_equal(a1, a2)
+    run = oracle.build_hierarchy(g, hec_mode=oracle.HEC_PAPER, seed=77)
+    lv = run.levels
+    for l in range(len(lv) - 1):
+        h = inputs.CSR(lv[l].n, lv[l].rowptr, lv[l].col, lv[l].w)
+        agg, nc = oracle.hec_paper(h, seed=77 + l)
+        assert np.array_equal(lv[l].agg, agg) and lv[l].nc == nc
+
+
+REFINES = [oracle.REFINE_LOBPCG, oracle.REFINE_LANCZOS]
+RTIGHT = dict(refine_tol=1e-9, refine_max_iters=200000)
+
+
+@pytest.mark.parametrize("refine", REFINES)
+def test_refine_path_and_grid_closed_forms(refine):
+    """Refined to a tight residual, lambda_2 and phi_2 of a path and of a
+    non-square unit grid match their closed forms."""
+    n = 60
+    r = oracle.solve(inputs.path(n), refine=refine, **RTIGHT)
+    assert r.status == 0 and r.level(0).pi_iters == 0 and r.refine_iters > 0
+    lam = 2 - 2 * np.cos(np.pi / n)
+    assert abs(r.lam - lam) <= 1e-12 * lam + 1e-15
+    v = np.cos(np.pi * (np.arange(n) + 0.5) / n)
+    assert angle(r.x(n), v) <= 1e-12
+    m, k = 40, 27
+    g = inputs.grid(m, k, "unit")
+    r = oracle.solve(g, refine=refine, **RTIGHT)
+    lam = 2 - 2 * np.cos(np.pi / m)
+    assert r.status == 0 and abs(r.lam - lam) <= 1e-12 * lam
+    v = np.cos(np.pi * (np.arange(g.n) // k + 0.5) / m)
+    assert angle(r.x(g.n), v) <= 1e-12
+
+
+@pytest.mark.parametrize("refine", REFINES)
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_refine_against_dense_jacobi(refine, seed):
+    """Random weighted graphs (n <= 200): the refined pair equals the dense
+    Jacobi eigenpair; the returned vector's residual, recomputed here, meets
+    the stop rule ||L x - theta x|| <= refine_tol theta ||x||."""
+    g = inputs.random_connected(170, 4.0, seed=seed)
+    ev, V, _ = oracle.jacobi_eig(laplacian_dense(g))
+    r = oracle.solve(g, refine=refine, refine_tol=1e-6, refine_max_iters=200000)
+    assert r.status == 0 and not r.capped
+    x = r.x(g.n)
+    Ld = laplacian_dense(g)
+    th = x @ Ld @ x
+    assert np.linalg.norm(Ld @ x - th * x) <= 1.001e-6 * th
+    assert abs(r.lam - ev[1]) <= 1e-10 * ev[1]
+    if ev[2] - ev[1] > 1e-3 * ev[1]:
+        assert 1 - abs(x @ V[:, 1]) <= 1e-9
+    r2 = oracle.solve(g, refine=refine, **RTIGHT)
+    assert abs(r2.lam - ev[1]) <= 1e-13 * ev[1]
+
+
+def test_refine_skewed_degrees():
+    """On a skewed-degree R-MAT graph the paper's stop rule leaves lambda_2 far
+    off, while both refinements reach the dense eigenvalue."""
+    g = inputs.rmat(8, seed=5)
+    ev = np.linalg.eigvalsh(laplacian_dense(g))
+    paper = oracle.solve(g)
+    assert paper.lam > 1.5 * ev[1]
+    its = {}
+    for refine in REFINES:
+        r = oracle.solve(g, refine=refine, refine_tol=1e-7, refine_max_iters=200000)
+        assert r.status == 0 and abs(r.lam - ev[1]) <= 1e-10 * ev[1], refine
+        its[refine] = r.refine_iters
+    # the D^-1 preconditioner evens out the spread of degrees: LOBPCG needs
+    # far fewer matvecs than the unpreconditioned Krylov method
+    assert its[oracle.REFINE_LOBPCG] * 5 < its[oracle.REFINE_LANCZOS]
+
+
+@pytest.mark.parametrize("refine", REFINES)
+def test_refine_forced_count_replays(refine):
+    """refine_forced = k runs exactly k matvecs; k = the free run's count gives
+    the free run's result bit for bit; one fewer gives a larger Rayleigh
+    quotient (the methods lower it monotonically)."""
+    g = inputs.grid(33, 19, "uniform", seed=12)
+    free = oracle.solve(g, refine=refine, refine_tol=1e-8, refine_max_iters=200000)
+    k = free.refine_iters
+    same = oracle.solve(g, refine=refine, refine_tol=1e-8, refine_forced=k)
+    assert same.refine_iters == k and same.lam == free.lam
+    assert np.array_equal(same.x(g.n), free.x(g.n))
+    if refine == oracle.REFINE_LOBPCG:
+        # the stop rule is tested before every step: the iterate one step
+        # earlier does not meet it (its residual, recomputed here, is too big)
+        less = oracle.solve(g, refine=refine, refine_tol=1e-8, refine_forced=k - 1)
+        assert less.refine_iters == k - 1 and less.lam > free.lam
+        Ld = laplacian_dense(g)
+        for run, ok in ((free, True), (less, False)):
+            x = run.x(g.n)
+            th = x @ Ld @ x
+            assert (np.linalg.norm(Ld @ x - th * x) <= 1e-8 * th) == ok
+    else:
+        # the Ritz estimate is tested at the end of each cycle: the cycle
+        # before the last one ends above the tolerance, the last one below
+        m = 24
+        assert k % m == 0 and k > m
+        Ld = laplacian_dense(g)
+        less = oracle.solve(g, refine=refine, refine_tol=1e-8, refine_forced=k - m)
+        for run, ok in ((free, True), (less, False)):
+            x = run.x(g.n)
+            th = x @ Ld @ x
+            assert (np.linalg.norm(Ld @ x - th * x) <= 1.001e-8 * th) == ok
+
+
+def test_refine_cap_and_degenerate_start():
+    """A cap below the needed count reports capped; on K_n (every vector of
+    1-perp an eigenvector) the refinement stops at once with lambda_2 = n."""
+    g = inputs.grid(30, 20, "uniform", seed=2)
+    r = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_tol=1e-12, refine_max_iters=3)
+    assert r.status == 0 and r.capped and r.refine_iters == 3
+    for refine in REFINES:
+        r = oracle.solve(inputs.complete(12), refine=refine)
+        assert r.status == 0 and abs(r.lam - 12) <= 1e-12 * 12
+        assert r.refine_iters <= 1
