@@ -74,7 +74,12 @@
  *           lanczos_basis steps;
  *       until ||L x - theta x|| <= refine_tol * theta * ||x|| (LOBPCG: tested
  *       before every step; Lanczos: the Ritz estimate beta_m |s_m| at the end
- *       of a cycle), or refine_max_iters matvecs.
+ *       of a cycle), or refine_max_iters matvecs.  LOBPCG also stops when the
+ *       Rayleigh quotient of the new iterate is not below the previous one:
+ *       in exact arithmetic each Rayleigh-Ritz step lowers it, so this only
+ *       happens at the rounding floor of the arithmetic (in float the residual
+ *       stalls near 1e-3 theta on graphs of small lambda_2 while lambda_2
+ *       itself is already exact to ~1e-8).
  */
 #include <math.h>
 #include <stdint.h>
@@ -916,7 +921,7 @@ static int refine_lobpcg(orc_level *lv, double *x, const oracle_opts *o) {
   }
   int forced = o->refine_forced, pvalid = 0, k = 0;
   lap_apply(L, x, lx);
-  double theta = vdot(n, x, lx) / vdot(n, x, x);
+  double theta = vdot(n, x, lx) / vdot(n, x, x), theta_prev = 0.0;
   for (;;) {
     double rr = 0.0;
     for (int i = 0; i < n; i++) {
@@ -924,8 +929,11 @@ static int refine_lobpcg(orc_level *lv, double *x, const oracle_opts *o) {
       rr += w[i] * w[i];
     }
     if (forced < 0 && sqrt(rr) <= o->refine_tol * theta * sqrt(vdot(n, x, x))) break;
+    /* stagnation: the Rayleigh quotient did not fall (rounding floor) */
+    if (forced < 0 && k > 0 && theta >= theta_prev) break;
     if (forced >= 0 && k >= forced) break;
     if (forced < 0 && k >= o->refine_max_iters) { lv->capped = 1; break; }
+    theta_prev = theta;
     for (int i = 0; i < n; i++) w[i] /= L->d[i];
     double mw = vsum(n, w) / (double)n;
     for (int i = 0; i < n; i++) w[i] -= mw;

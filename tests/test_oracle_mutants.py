@@ -71,6 +71,8 @@ MUTANTS = [
      "for (int i = 0; i < m; i++) y += Rinv[i][a] * V[i * m + (m - 1)];"),
     ("lobpcg_stop_rule_absolute", "sqrt(rr) <= o->refine_tol * theta * sqrt(vdot(n, x, x))",
      "sqrt(rr) <= o->refine_tol * sqrt(vdot(n, x, x))"),
+    ("lobpcg_stall_rule_loose", "if (forced < 0 && k > 0 && theta >= theta_prev) break;",
+     "if (forced < 0 && k > 0 && theta >= theta_prev * (1.0 - 1e-3)) break;"),
     ("lanczos_alpha_halved", "      al[j] = vdot(n, q, u);\n", "      al[j] = 0.5 * vdot(n, q, u);\n"),
     ("lanczos_largest_ritz_vector", "y += V[t * kk + 0] * Q[(size_t)t * n + i];",
      "y += V[t * kk + (kk - 1)] * Q[(size_t)t * n + i];"),
