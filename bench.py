@@ -90,6 +90,67 @@ def ncu_traffic(kernel):
     return None if k is None else k.get("dram_bytes_per_launch")
 
 
+def host_cpu():
+    """Host CPU model and logical core count (the oracle's timings run there)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    model = v
+                    break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"model": model or platform.processor() or "unknown", "arch": platform.machine(),
+            "logical_cores": os.cpu_count()}
+
+
+# Algorithmic bytes of the method, per the scope table's measurement model:
+#  * one Gauss-Seidel sweep or power-iteration matvec on a level:
+#      B_sweep = 4(n+1) + (4 + V) nnz + 2 V n   (V = value bytes; FP32: 12n + 16E)
+#  * one "pass over nnz" of the setup: P = 4(n+1) + (4 + w) nnz, w = setup
+#    weight bytes (the caller's float on the fine level, FP64 on coarse levels);
+#    a coarsened level takes 4 passes (colouring, matching, Galerkin, solve-order
+#    copy), the fine level one more (ingest), the coarsest level 2 (colouring,
+#    copy);
+#  * the Rayleigh quotient: one B_sweep on the fine level.
+# Implementation bytes (worklists, sorts, scratch) are not counted.
+def algorithmic_bytes(plan, fp64, w_bytes0=4, tail_max_n=4096, tail_max_nnz=32768):
+    """Per-kernel algorithmic bytes of the last solve: {"grid_setup", "cta",
+    "grid_solve"}, plus the split of grid_solve into Gauss-Seidel/power iteration."""
+    out = {"grid_setup": 0.0, "cta": 0.0, "grid_solve": 0.0, "grid_sweeps": 0.0}
+    nl = plan.num_levels
+    for l in range(nl):
+        li = plan.level_info(l)
+        n, nnz = float(li.n), float(li.nnz)
+        tiny = li.n <= 256 and li.nnz <= 4096
+        small = tiny or (li.n <= tail_max_n and li.nnz <= tail_max_nnz)
+        v = 8.0 if (fp64 or tiny) else 4.0
+        wb = float(w_bytes0) if l == 0 else 8.0
+        p = 4.0 * (n + 1) + (4.0 + wb) * nnz
+        passes = 2 if l == nl - 1 else (5 if l == 0 else 4)
+        sweep = 4.0 * (n + 1) + (4.0 + v) * nnz + 2.0 * v * n
+        sweeps = (li.gs_sweeps + li.pi_iters) * sweep + (sweep if l == 0 else 0.0)
+        if small:
+            out["cta"] += passes * p + sweeps
+        else:
+            out["grid_setup"] += passes * p
+            out["grid_solve"] += sweeps
+            out["grid_sweeps"] += (li.gs_sweeps + li.pi_iters) * sweep
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks sampled during the timed region."""
 
@@ -158,9 +219,11 @@ def batch_name(count):
 
 def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15, dist=None):
     """The batched form on the batch workload: one fiedler_solve_batch call per
-    step over all graphs (device-resident inputs and outputs), FP32 form; the
-    plain single-graph FP64 form on every plain_every-th graph for solves/s and
-    lambda2 agreement; the batched FP64 form once over the whole batch."""
+    step over all graphs (device-resident inputs and outputs), FP32 form, in
+    two settings: the paper's stop rule, and the finest-level LOBPCG
+    refinement (refine_tol 1e-4).  For each: the batched FP64 form once over
+    the whole batch, and the plain single-graph FP64 form on every
+    plain_every-th graph, for solves/s and lambda_2 agreement."""
     import torch
     from paper_1602_04386_gb300 import fiedler
     count = len(graphs)
@@ -177,6 +240,8 @@ def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15, dist=Non
     X = torch.empty(off, dtype=torch.float64, device=dev)
     base = X.data_ptr()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak, peak_kind = measured_peaks()
+    fam = np.array([0 if g.name.startswith("grid") else 1 for g in graphs])
 
     def run_batch(plan):
         for i in range(count):
@@ -194,90 +259,183 @@ def batched_leg(graphs, stream, dev, steps=3, warmup=1, plain_every=15, dist=Non
             raise fiedler.FiedlerError(st, "fiedler_solve_batch")
         return e0.elapsed_time(e1), wall
 
-    plan = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP32_FP64RED)
-    # autotuner: block size per graph chosen on every 3rd graph of the batch
-    # (both families: the stride is odd), a third of the batch's mix of sizes
-    tsample = (fiedler.fiedler_graph * len(range(0, count, 3)))()
-    for k, i in enumerate(range(0, count, 3)):
-        tsample[k] = garr[i]
-    st, tuning = fiedler.fiedler_plan_autotune(plan.h, tsample)
-    if st != fiedler.FIEDLER_OK:
-        raise fiedler.FiedlerError(st, "fiedler_plan_autotune")
-    for _ in range(warmup):
-        run_batch(plan)
-    plan.set_profiling(True)
-    ms, walls, kms, kbytes, launches = [], [], 0.0, 0.0, 0
-    for _ in range(steps):
-        t, wall = run_batch(plan)
-        ms.append(t)
-        walls.append(wall)
-        pr = plan.profile()
-        pr_name = pr.kernel_name[3].decode()
-        kms += pr.kernel_ms[3]
-        kbytes += pr.kernel_bytes[3]
-        launches += int(pr.kernel_launches)
-    plan.set_profiling(False)
-    lam32 = np.array([rarr[i].lambda2 for i in range(count)])
-    st32 = np.array([rarr[i].status for i in range(count)])
-    plan.close()
-    # batched FP64 form, one pass
-    plan64b = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP64)
-    t64b, _ = run_batch(plan64b)
-    lam64b = np.array([rarr[i].lambda2 for i in range(count)])
-    st64b = np.array([rarr[i].status for i in range(count)])
-    plan64b.close()
-    # plain single-graph FP64 form on a sample
-    plan64 = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP64)
-    sample = list(range(0, count, plain_every))
-    lam64 = {}
-    plan64.solve_struct(garr[sample[0]], X[offs[sample[0]]:], x_on_device=True)
-    flush.zero_()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in sample:
-        r = plan64.solve_struct(garr[i], X[offs[i]:], x_on_device=True)
-        lam64[i] = (r.status, r.lambda2)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t64 = e0.elapsed_time(e1)
-    plan64.close()
-    ok = [i for i in sample if st32[i] == 0 and lam64[i][0] == 0]
-    rel = np.array([abs(lam32[i] - lam64[i][1]) / abs(lam64[i][1]) for i in ok])
-    fam = np.array([0 if graphs[i].name.startswith("grid") else 1 for i in ok])
-    okb = (st32 == 0) & (st64b == 0)
-    relb = np.abs(lam32[okb] - lam64b[okb]) / np.abs(lam64b[okb])
-
     def agree(r):
         if r.size == 0:
             return None
         return {"max": float(r.max()), "median": float(np.median(r)), "frac_le_1e-5": float((r <= 1e-5).mean()),
                 "graphs": int(r.size)}
-    ms_step = shard.reduce_max(statistics.mean(ms), dist, dev)  # the slowest rank's batch time
-    total = shard.reduce_sum(count, dist, dev)
+
+    # autotuner: block size per graph chosen on every 3rd graph of the batch
+    # (both families: the stride is odd), a third of the batch's mix of sizes
+    tsample = (fiedler.fiedler_graph * len(range(0, count, 3)))()
+    for k, i in enumerate(range(0, count, 3)):
+        tsample[k] = garr[i]
+
+    def one_setting(kw, tune):
+        tuning = None
+        if tune:
+            plan = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP32_FP64RED, **kw)
+            st, tuning = fiedler.fiedler_plan_autotune(plan.h, tsample)
+            if st != fiedler.FIEDLER_OK:
+                raise fiedler.FiedlerError(st, "fiedler_plan_autotune")
+        else:  # the block size the first setting's autotuner chose
+            plan = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP32_FP64RED,
+                                batch_threads=tune_threads[0], **kw)
+        for _ in range(warmup):
+            run_batch(plan)
+        plan.set_profiling(True)
+        ms, walls, kms, kbytes, launches = [], [], 0.0, 0.0, 0
+        for _ in range(steps):
+            t, wall = run_batch(plan)
+            ms.append(t)
+            walls.append(wall)
+            pr = plan.profile()
+            pr_name = pr.kernel_name[3].decode()
+            kms += pr.kernel_ms[3]
+            kbytes += pr.kernel_bytes[3]
+            launches += int(pr.kernel_launches)
+        plan.set_profiling(False)
+        lam32 = np.array([rarr[i].lambda2 for i in range(count)])
+        st32 = np.array([rarr[i].status for i in range(count)])
+        rit = np.array([rarr[i].refine_iters for i in range(count)])
+        plan.close()
+        # batched FP64 form, one pass
+        plan64b = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP64, **kw)
+        t64b, _ = run_batch(plan64b)
+        lam64b = np.array([rarr[i].lambda2 for i in range(count)])
+        st64b = np.array([rarr[i].status for i in range(count)])
+        plan64b.close()
+        # plain single-graph FP64 form on a sample
+        plan64 = fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP64, **kw)
+        sample = list(range(0, count, plain_every))
+        lam64 = {}
+        plan64.solve_struct(garr[sample[0]], X[offs[sample[0]]:], x_on_device=True)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in sample:
+            r = plan64.solve_struct(garr[i], X[offs[i]:], x_on_device=True)
+            lam64[i] = (r.status, r.lambda2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        plan64.close()
+        ok = [i for i in sample if st32[i] == 0 and lam64[i][0] == 0]
+        rel = np.array([abs(lam32[i] - lam64[i][1]) / abs(lam64[i][1]) for i in ok])
+        famo = fam[ok]
+        okb = (st32 == 0) & (st64b == 0)
+        relb = np.abs(lam32[okb] - lam64b[okb]) / np.abs(lam64b[okb])
+        ms_step = shard.reduce_max(statistics.mean(ms), dist, dev)  # the slowest rank's batch time
+        total = shard.reduce_sum(count, dist, dev)
+        kgbs = kbytes / (kms / 1e3) / 1e9 if kms > 0 else None
+        # the plain form's solves/s is scaled to the whole batch by vertex +
+        # nonzero count: the sample took t64, the batch would take t64 * scale
+        size = np.array([g.n + g.nnz for g in graphs], dtype=np.float64)
+        scale = size.sum() / size[sample].sum()
+        out = {
+            "solves_per_s": total / (ms_step / 1e3), "ms_per_batch": ms_step, "graphs_all_ranks": int(total),
+            "wall_ms_per_batch": 1e3 * statistics.mean(walls), "statuses_ok": int((st32 == 0).sum()),
+            "statuses": {str(k): int(v) for k, v in zip(*np.unique(st32, return_counts=True))},
+            "kernel": pr_name, "kernel_ms": kms / steps, "gpu_launches_per_batch": launches / steps,
+            "kernel_implementation_gbs": kgbs, "peak_kind": f"of {peak_kind}",
+            "refine_iters": {"mean": float(rit.mean()), "max": int(rit.max())},
+            "fp64_batched_solves_per_s": count / (t64b / 1e3),
+            "fp64_plain_solves_per_s": count / ((t64 / 1e3) * scale),
+            "fp64_plain_sample": f"every {plain_every}th graph ({len(sample)}), time scaled by (n+nnz) to the batch",
+            "lambda2_rel_err_vs_fp64_plain": {"all": agree(rel), "grids": agree(rel[famo == 0]),
+                                              "rmat": agree(rel[famo == 1])},
+            "lambda2_rel_err_vs_fp64_batched": agree(relb),
+            "fp64_batched_statuses_ok": int((st64b == 0).sum()),
+        }
+        return out, tuning
+
+    tune_threads = [512]
+    paper, tuning = one_setting({}, True)
+    tune_threads[0] = tuning.batch_threads
+    refined, _ = one_setting({"refine": fiedler.FIEDLER_REFINE_LOBPCG, "refine_tol": 1e-4}, False)
     nnz = int(sum(g.nnz for g in graphs))
-    peak, peak_kind = measured_peaks()
-    kgbs = kbytes / (kms / 1e3) / 1e9 if kms > 0 else None
-    # weight of the sample: the solves/s of the plain form is scaled to the
-    # whole batch by vertex + nonzero count
-    size = np.array([g.n + g.nnz for g in graphs], dtype=np.float64)
-    scale = size.sum() / size[sample].sum()
-    return {
+    out = {
         "workload": batch_name(count), "graphs": count, "vertices": int(sum(g.n for g in graphs)), "nnz": nnz,
         "form": "FP32 values/matvec, FP64 reductions; one persistent launch per call",
-        "autotune": {"batch_threads": tuning.batch_threads, "sample_ms_512_256_128": [round(x, 2) for x in tuning.batch_ms],
+        "autotune": {"batch_threads": tuning.batch_threads,
+                     "sample_ms_512_256_128": [round(x, 2) for x in tuning.batch_ms],
                      "sample": f"every 3rd graph ({len(tsample)})"},
-        "solves_per_s": total / (ms_step / 1e3), "ms_per_batch": ms_step, "graphs_all_ranks": int(total), "wall_ms_per_batch": 1e3 * statistics.mean(walls),
-        "statuses_ok": int((st32 == 0).sum()),
-        "kernel": pr_name, "kernel_ms": kms / steps, "gpu_launches_per_batch": launches / steps,
-        "kernel_algorithmic_gbs": kgbs, "kernel_frac": (kgbs / peak) if kgbs else None, "peak_kind": f"of {peak_kind}",
-        "fp64_batched_solves_per_s": count / (t64b / 1e3),
-        "fp64_plain_solves_per_s": len(sample) / (t64 / 1e3) / scale,
-        "fp64_plain_sample": f"every {plain_every}th graph ({len(sample)}), rate scaled by (n+nnz) to the batch",
-        "lambda2_rel_err_vs_fp64_plain": {"all": agree(rel), "grids": agree(rel[fam == 0]),
-                                          "rmat": agree(rel[fam == 1])},
-        "lambda2_rel_err_vs_fp64_batched": agree(relb),
-        "fp64_batched_statuses_ok": int((st64b == 0).sum()),
+        "refined_lobpcg_1e-4": refined,
     }
+    out.update(paper)
+    return out
+
+
+def timed_solves(plan, g, stream, dev, steps, warmup, flush):
+    """Solves g `steps` times on plan (device-resident inputs and output, L2
+    flushed between solves, CUDA events on the plan's stream); returns
+    (mean ms, last result, edge sweeps of one solve)."""
+    import torch
+    from paper_1602_04386_gb300 import fiedler
+    gs, keep = fiedler.device_graph(g, dev)
+    x = torch.empty(g.n, dtype=torch.float64, device=dev)
+    r = None
+    for _ in range(warmup):
+        flush.zero_()
+        r = plan.solve_struct(gs, x, x_on_device=True)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = plan.solve_struct(gs, x, x_on_device=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    if r.status not in (fiedler.FIEDLER_OK, fiedler.FIEDLER_ENOTCONVERGED):
+        raise fiedler.FiedlerError(r.status, f"fiedler_solve ({g.name})")
+    sweeps = 0
+    for l in range(plan.num_levels):
+        li = plan.level_info(l)
+        sweeps += int(li.nnz) * (li.gs_sweeps + li.pi_iters + li.refine_iters)
+    del keep
+    return statistics.mean(ms), r, sweeps
+
+
+def configs_leg(stream, dev, steps=5, warmup=2):
+    """The other single-graph workloads: the 64 x 48 unit grid in the plain FP64
+    form (lambda_2 against its closed form), the linear-complexity sweep of
+    weighted grids 256x192 .. 2048x1536 in the FP32 form (solves/s, edge
+    sweeps/s, least-squares fit of time against n), and the 200,000-point
+    Gaussian-mixture kNN graph in the FP32 form, with the paper's stop rule
+    and with the finest-level LOBPCG refinement."""
+    import torch
+    from paper_1602_04386_gb300 import fiedler
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    g1 = inputs.grid(64, 48, "unit")
+    with fiedler.Plan(stream=stream.cuda_stream, precision=fiedler.FIEDLER_FP64) as p:
+        ms, r, sw = timed_solves(p, g1, stream, dev, 20, 3, flush)
+    lam = 2 - 2 * np.cos(np.pi / 64)
+    out["grid64x48_unit_fp64"] = {"solves_per_s": 1e3 / ms, "ms": ms, "lambda2": r.lambda2,
+                                  "lambda2_closed_form": lam, "rel_err_vs_closed_form": abs(r.lambda2 - lam) / lam,
+                                  "levels": r.levels}
+    sweep = []
+    with fiedler.Plan(stream=stream.cuda_stream) as p:
+        for m, k in ((256, 192), (512, 384), (1024, 768), (2048, 1536)):
+            g = inputs.grid(m, k, "uniform", seed=inputs.BASE_SEED + 2)
+            ms, r, sw = timed_solves(p, g, stream, dev, steps, warmup, flush)
+            sweep.append({"grid": f"{m}x{k}", "n": g.n, "nnz": g.nnz, "ms": ms, "solves_per_s": 1e3 / ms,
+                          "edge_sweeps_per_s": sw / (ms / 1e3), "lambda2": r.lambda2, "levels": r.levels})
+    n = np.array([e["n"] for e in sweep], dtype=np.float64)
+    t = np.array([e["ms"] for e in sweep])
+    slope, icpt = np.polyfit(n, t, 1)
+    out["grid_sweep_fp32"] = {"sizes": sweep, "fit_ms": {"per_vertex_ns": slope * 1e6, "intercept_ms": icpt,
+                                                         "r": float(np.corrcoef(n, t)[0, 1])}}
+    g3 = inputs.knn_mixture(200000)
+    knn = {"n": g3.n, "nnz": g3.nnz}
+    for name, kw in (("paper_stop_rule", {}), ("lobpcg_refined", {"refine": fiedler.FIEDLER_REFINE_LOBPCG})):
+        with fiedler.Plan(stream=stream.cuda_stream, **kw) as p:
+            ms, r, sw = timed_solves(p, g3, stream, dev, steps, warmup, flush)
+        knn[name] = {"solves_per_s": 1e3 / ms, "ms": ms, "lambda2": r.lambda2, "residual": r.residual,
+                     "refine_iters": r.refine_iters, "status": r.status, "edge_sweeps_per_s": sw / (ms / 1e3)}
+    out["knn200000_fp32"] = knn
+    return out
 
 
 SERVE = dict(rate=2000.0, seconds=3.0, pool=24, nmin=1e3, nmax=2e6, seed=inputs.BASE_SEED + 5)
@@ -417,35 +575,34 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None)
 
 
 def run_reference(args):
-    """The oracle, as it stands, on the host cores: each step solves a quarter-size
-    sample of the workload (1024 x 768 grid of the same family) and is scaled to
-    the full workload by its nonzero count (the method is linear in the graph size)."""
+    """The oracle, as it stands, on the host cores: each step is one whole solve
+    of the workload itself (the 2048 x 1536 grid, single-threaded C, FP64)."""
     import oracle
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    full = make_graph()
-    samp_w = dict(WORKLOAD, m=WORKLOAD["m"] // 2, k=WORKLOAD["k"] // 2)
-    g = make_graph(samp_w)
-    scale = full.nnz / g.nnz
+    g = make_graph()
+    oracle.build()
     for _ in range(args.warmup):
         oracle.solve(g)
     t = []
+    lam = None
     for _ in range(args.steps):
         t0 = time.perf_counter()
         r = oracle.solve(g)
         t.append(time.perf_counter() - t0)
         assert r.status == 0
-    sec_full = statistics.mean(t) * scale
-    value = 1.0 / sec_full
+        lam = r.lam
+    sec = statistics.mean(t)
+    value = 1.0 / sec
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_full * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(), "n": full.n, "nnz": full.nnz},
+        "config": {"workload": workload_name(), "n": g.n, "nnz": g.nnz, "edges": g.nnz // 2},
         "cpu_baseline": {"kind": "oracle", "value": value, "unit": "solves/s", "cores": 1,
-                         "sample": f"{workload_name(samp_w)} per step (nnz {g.nnz}), time x {scale:.3f} "
-                                   f"(nnz ratio to the full workload)"},
+                         "sample": f"one whole solve of {workload_name()} per step (single-threaded C, FP64)",
+                         "host": host_cpu(), "lambda2": lam},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -463,6 +620,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form leg")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"])
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-form leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other single-graph workloads")
     ap.add_argument("--serve-rate", type=float, default=SERVE["rate"])
     ap.add_argument("--serve-seconds", type=float, default=SERVE["seconds"])
     args = ap.parse_args()
@@ -560,10 +718,17 @@ def main():
     ms_per_step = tot_ms / args.steps
     value = ws * args.steps / (tot_ms / 1e3)
 
-    # roofline of the dominant kernel (most device time in the timed steps)
+    # roofline of the dominant kernel (most device time in the timed steps):
+    # algorithmic bytes of the measurement model (algorithmic_bytes) per launch
+    # over the kernel's mean CUDA-event time on the plan's stream; the engine's
+    # own byte count (worklists, sorts, copies) is kept beside it
     peak, peak_kind = measured_peaks()
     dom = max(kms, key=lambda k: kms[k])
-    achieved = kbytes[dom] / (kms[dom] / 1e3) / 1e9
+    alg = algorithmic_bytes(plan, prec == fiedler.FIEDLER_FP64)
+    kslot = {pr.kernel_name[k].decode(): ("grid_setup", "cta", "grid_solve")[k] for k in range(3)}
+    alg_dom = alg[kslot[dom]]
+    dom_ms = kms[dom] / klaunch[dom]
+    achieved = alg_dom / (dom_ms / 1e3) / 1e9
     phase_names = [pr.phase_name[i].decode() for i in range(pr.n_phases)]
     gi, pi_ = phase_names.index("gauss_seidel"), phase_names.index("power_iter")
     sg_bytes = ph_bytes[0][gi] + ph_bytes[0][pi_]
@@ -589,11 +754,20 @@ def main():
         "edge_sweeps_per_s": None,
         "gpu_launches": launches,
         "kernels": {k: {"launches": klaunch[k], "ms_per_step": kms[k] / args.steps,
-                        "gbs": kbytes[k] / (kms[k] / 1e3) / 1e9 if kms[k] > 0 else None} for k in kms},
+                        "algorithmic_bytes": alg[kslot[k]],
+                        "algorithmic_gbs": alg[kslot[k]] / (kms[k] / klaunch[k] / 1e3) / 1e9 if kms[k] > 0 else None,
+                        "implementation_bytes": kbytes[k] / klaunch[k],
+                        "implementation_gbs": kbytes[k] / (kms[k] / 1e3) / 1e9 if kms[k] > 0 else None}
+                    for k in kms},
         "phase_ms_per_step": phases,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
-                     "traffic": ncu_traffic(dom), "algorithmic_bytes_per_launch": kbytes[dom] / klaunch[dom]},
+                     "traffic": ncu_traffic(dom), "algorithmic_bytes_per_launch": alg_dom,
+                     "kernel_ms_per_launch": dom_ms,
+                     "bytes_model": "setup: 5 passes 4(n+1)+(4+w)nnz on the fine level, 4 on coarsened levels, "
+                                    "2 on the coarsest; solve: (gs+pi) x (4(n+1)+(4+V)nnz+2Vn) per level, "
+                                    "+1 on the fine level (Rayleigh quotient)",
+                     "implementation_bytes_per_launch": kbytes[dom] / klaunch[dom]},
     }
     # edge-sweeps: nnz (= 2E) entries per Gauss-Seidel sweep or power-iteration matvec, all levels
     sweeps = 0
@@ -666,7 +840,7 @@ def main():
             tc = time.perf_counter() - t0
             line["cpu_baseline"] = {"value": nrep / tc, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                     "sample": f"{nrep} whole solves of {workload_name()} (single-threaded C)",
-                                    "lambda2": ro.lam}
+                                    "host": host_cpu(), "lambda2": ro.lam}
     plan.close()
 
     def extra_leg(name, fn):
@@ -681,6 +855,8 @@ def main():
             print(f"bench: {name} leg failed: {e!r}", file=sys.stderr)
             return {"error": f"{type(e).__name__}: {e}"}
 
+    if not args.no_configs:
+        line["configs"] = extra_leg("configs", lambda: configs_leg(stream, dev))
     if batch_graphs is not None:
         line["batched"] = extra_leg("batched", lambda: batched_leg(batch_graphs, stream, dev, dist=dist))
         if "gpu_launches_per_batch" in line["batched"]:

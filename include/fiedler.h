@@ -59,6 +59,25 @@ enum { FIEDLER_FP64 = 0, FIEDLER_FP32_FP64RED = 1 };
 enum { FIEDLER_TIE_HASHED = 0, FIEDLER_TIE_INDEX = 1 };
 /* fiedler_graph.w_dtype */
 enum { FIEDLER_W_F32 = 0, FIEDLER_W_F64 = 1 };
+/* fiedler_options.refine: what runs on the finest level after its Gauss-Seidel
+ * sweeps.  NONE is the method as the paper states it (power iteration on
+ * sigma I - L, stopped by the cosine test of Sec. 3).  The two Krylov
+ * eigensolvers replace that power iteration on the finest level only and run
+ * until the eigen-residual is below refine_tol (Sec. 4 proposes a Lanczos
+ * smoother as future work; the cosine test stops power iteration long before
+ * the residual is small on graphs with a wide spread of degrees):
+ *  - LOBPCG: single-vector locally optimal preconditioned conjugate gradient
+ *    (Knyazev, 2001) on 1-perp, preconditioned by the inverse degree D^-1;
+ *  - LANCZOS: Lanczos with full reorthogonalisation on 1-perp, restarted from
+ *    the Ritz vector every lanczos_basis steps. */
+enum { FIEDLER_REFINE_NONE = 0, FIEDLER_REFINE_LOBPCG = 1, FIEDLER_REFINE_LANCZOS = 2 };
+/* fiedler_options.hec_mode: heavy-edge coarsening rule (Alg. 1).  DOMINANT:
+ * the deterministic locally dominant matching under the order of tie_rule
+ * (default).  PAPER: Alg. 1 as printed, vertices visited in a seeded random
+ * order, each unaggregated vertex pairing with its heaviest neighbour or
+ * joining that neighbour's aggregate; the order on level l is the ascending
+ * order of the keys splitmix64(seed + l, v) (ties by v). */
+enum { FIEDLER_HEC_DOMINANT = 0, FIEDLER_HEC_PAPER = 1 };
 
 typedef struct {
   int precision;             /* FIEDLER_FP64: values and arithmetic in double.
@@ -92,6 +111,13 @@ typedef struct {
   int batch_threads;         /* batched and serving forms: threads per graph's block, 512, 256 or
                                 128 (1, 2 or 4 graphs per SM); 0 = 512 until fiedler_plan_autotune
                                 picks one */
+  int refine;                /* FIEDLER_REFINE_NONE (default), _LOBPCG or _LANCZOS (see above) */
+  int refine_max_iters;      /* cap on the finest level's Krylov matvecs; reaching it gives
+                                FIEDLER_ENOTCONVERGED with the result filled */
+  double refine_tol;         /* Krylov stop: ||L x - theta x|| <= refine_tol * theta * ||x||,
+                                theta = x^T L x / x^T x */
+  int lanczos_basis;         /* FIEDLER_REFINE_LANCZOS: basis vectors per restart cycle, 4..64 */
+  int hec_mode;              /* FIEDLER_HEC_DOMINANT (default) or FIEDLER_HEC_PAPER */
 } fiedler_options;
 
 typedef struct {
@@ -120,6 +146,7 @@ typedef struct {
                                 graph's own block time on the device timer (batched form) */
   long long bad_index;       /* first offending position when status == FIEDLER_EINVAL, else -1 */
   fiedler_status status;     /* same value as returned */
+  int refine_iters;          /* Krylov matvecs on the finest level (0 with FIEDLER_REFINE_NONE) */
 } fiedler_result;
 
 typedef struct fiedler_plan fiedler_plan;
@@ -129,7 +156,8 @@ typedef struct fiedler_plan fiedler_plan;
  * 100000, pi_cos_tol 1e-6, resid_tol 0, hashed ties, seed 20160214,
  * validate 1, tail_max_n 4096, tail_max_nnz 32768, barrier_timeout_ms 5000, fault_inject 0,
  * hbm_budget_bytes 0 (16 GiB), max_batch 1024, queue_budget_bytes 0 (8 GiB),
- * batch_threads 0. */
+ * batch_threads 0, refine NONE, refine_max_iters 5000, refine_tol 1e-4,
+ * lanczos_basis 24, hec_mode DOMINANT. */
 void fiedler_options_default(fiedler_options *opts);
 
 /* Creates a plan on the current CUDA device.  opts may be NULL (defaults);
@@ -216,6 +244,7 @@ typedef struct {
   double last_cos;           /* (u^k, u^{k-1}) of the last power iteration */
   float phase_ms[16];        /* device time spent on this level per phase, in the order of
                                 fiedler_profile.phase_name (device timer) */
+  int refine_iters;          /* Krylov matvecs on this level (finest level only) */
 } fiedler_level_info;
 
 /* Number of levels of the last solve (0 before any solve). */
@@ -308,9 +337,13 @@ fiedler_status fiedler_plan_get_profile(const fiedler_plan *plan, fiedler_profil
  *  - Every call reuses the same array and overwrites the previous call's
  *    contents (the state is rewritten at the start of each call), so calls must
  *    not overlap on the GPU: the library serialises callers within a process.
+ *  - Not for stream capture: every call reads host memory and ends in a
+ *    synchronisation of cuda_stream, so a call on a stream that is capturing
+ *    returns FIEDLER_EINVAL without queueing work.
  *  - The first call on each device looks up the array's device address with
- *    cudaGetSymbolAddress (with that device current); make that first call
- *    before any stream capture begins.
+ *    cudaGetSymbolAddress (with that device current).
+ *  - Options are checked as fiedler_plan_create checks them; a refused call
+ *    sets result->status (and bad_index = -1) when result is given.
  *  - Every level runs in the one-block engine, so results equal those of
  *    fiedler_solve with tail_max_n at least n and tail_max_nnz at least nnz. */
 fiedler_status fiedler_solve_noalloc(const fiedler_options *opts, const fiedler_graph *graph, double *x,

@@ -26,6 +26,7 @@
 
 #include "fiedler.h"
 #include "fz_state.h"
+#include "host_opts.h"
 #include "kernels.h"
 
 using fz::State;
@@ -196,7 +197,7 @@ fiedler_status ensure(fiedler_plan *p, void **ptr, size_t *cap, size_t bytes) {
   return FIEDLER_OK;
 }
 
-size_t arena_estimate(int64_t n, int64_t nnz, size_t tsz, bool wf64) {
+size_t arena_estimate(int64_t n, int64_t nnz, size_t tsz, bool wf64, const fiedler_options &o) {
   // fine level: optional self-loop-free copy, degree, matching, aggregates,
   // colours, permutations, colour-order copy, iterates
   double l0 = 4.0 * (n + 1) + (4.0 + (wf64 ? 8.0 : 4.0)) * nnz + 8.0 * n + 4.0 * n * 3 + 8.0 * n +
@@ -206,15 +207,19 @@ size_t arena_estimate(int64_t n, int64_t nnz, size_t tsz, bool wf64) {
                      (2.0 * tsz + 4.0) * n) +
               fz::kMaxLevels * 4.0 * (fz::kMaxColors + 1);
   double slack = fz::kMaxLevels * 24.0 * 256.0 + (1 << 20);
-  return (size_t)(l0 + lc + slack);
+  return (size_t)(l0 + lc + slack) + fz::refine_bytes(n, tsz, o.refine, o.lanczos_basis);
 }
 
-size_t scratch_estimate(int64_t n, int64_t nnz, int nblocks) {
+size_t scratch_estimate(int64_t n, int64_t nnz, int nblocks, const fiedler_options &o) {
   // one level's scratch, all live at once: colouring (cround + 3 worklists +
   // heavy list + resume positions), matching (cand + 3 worklists + heavy list), Galerkin (9 per-vertex / per-aggregate
   // arrays, (J, slot) keys + FP64 weights per cross entry), colour histogram
   double b = 24.0 * n + 20.0 * n + 4.0 * (n + 1) * 9 + 16.0 * nnz + 4.0 * fz::kMaxColors * nblocks +
              64.0 * 256.0 + (1 << 20);
+  // Alg. 1's random-order greedy (hec_mode PAPER) keeps more per-vertex state
+  // than the matching: heaviest neighbour, turn state, first claimant (key and
+  // vertex), labels, founder ids and the founders' buckets
+  if (o.hec_mode == FIEDLER_HEC_PAPER) b += 44.0 * n + 8.0 * 256.0;
   return (size_t)b;
 }
 
@@ -230,6 +235,23 @@ fiedler_status map_status(int st) {
     case fz::ST_ENOTSUP: return FIEDLER_ENOTSUP;
     default: return FIEDLER_ECUDA;
   }
+}
+
+}  // namespace
+
+namespace fz {
+
+bool options_valid(const fiedler_options &o) {
+  return !((o.precision != FIEDLER_FP64 && o.precision != FIEDLER_FP32_FP64RED) || o.coarse_max_n < 1 ||
+           o.max_levels < 1 || o.max_levels > fz::kMaxLevels || !(o.stall_ratio > 0.0 && o.stall_ratio <= 1.0) ||
+           o.gs_sweeps < 0 || o.pi_max_iters < 0 || o.pi_max_iters_coarsest < 0 || !(o.pi_cos_tol >= 0.0) ||
+           !(o.resid_tol >= 0.0) || (o.tie_rule != 0 && o.tie_rule != 1) || o.tail_max_n < 1 ||
+           o.tail_max_nnz < 1 || o.barrier_timeout_ms < 1 || o.max_batch < 1 ||
+           (o.batch_threads != 0 && o.batch_threads != 512 && o.batch_threads != 256 && o.batch_threads != 128) ||
+           (o.refine != FIEDLER_REFINE_NONE && o.refine != FIEDLER_REFINE_LOBPCG &&
+            o.refine != FIEDLER_REFINE_LANCZOS) ||
+           o.refine_max_iters < 0 || !(o.refine_tol > 0.0 && o.refine_tol < 1.0) || o.lanczos_basis < 4 ||
+           o.lanczos_basis > fz::kMaxBasis || (o.hec_mode != FIEDLER_HEC_DOMINANT && o.hec_mode != FIEDLER_HEC_PAPER));
 }
 
 void fill_opts(fz::Opts &o, const fiedler_options &u, int type) {
@@ -252,10 +274,21 @@ void fill_opts(fz::Opts &o, const fiedler_options &u, int type) {
   o.guard = type == 0 ? ldexp(1.0, -20) : ldexp(1.0, -16);
   o.seed = u.seed;
   o.barrier_timeout_ns = (unsigned long long)u.barrier_timeout_ms * 1000000ull;
+  o.refine = u.refine;
+  o.refine_max_iters = u.refine_max_iters;
+  o.lanczos_basis = u.lanczos_basis;
+  o.hec_mode = u.hec_mode;
+  o.refine_tol = u.refine_tol;
 }
 
+}  // namespace fz
+
+namespace {
+
+using fz::fill_opts;
+
 const char *kPhaseNames[fz::PH_COUNT] = {"ingest", "colour", "reorder", "match", "aggregate", "galerkin",
-                                         "coarsest", "prolong", "gauss_seidel", "power_iter", "final"};
+                                         "coarsest", "prolong", "gauss_seidel", "power_iter", "final", "refine"};
 
 fiedler_status launch(fiedler_plan *p, const void *fn, int grid, int block, bool coop, int slot) {
   void *args[] = {(void *)&p->d_state};
@@ -276,8 +309,8 @@ fiedler_status run_solve(fiedler_plan *p, int64_t n, int64_t nnz, const int32_t 
   const fz::KernelSet &K = p->ks[type];
   const int gmax = p->grid_blocks[type][0] > p->grid_blocks[type][1] ? p->grid_blocks[type][0]
                                                                        : p->grid_blocks[type][1];
-  size_t abytes = arena_estimate(n, nnz, tsz, w_f64 != 0);
-  size_t sbytes = scratch_estimate(n, nnz, gmax);
+  size_t abytes = arena_estimate(n, nnz, tsz, w_f64 != 0, p->opt);
+  size_t sbytes = scratch_estimate(n, nnz, gmax, p->opt);
   fiedler_status st = FIEDLER_OK;
   for (int attempt = 0; attempt < 4; attempt++) {
     if ((st = ensure(p, (void **)&p->d_arena, &p->arena_cap, abytes)) != FIEDLER_OK) return st;
@@ -368,6 +401,7 @@ fiedler_status run_solve(fiedler_plan *p, int64_t n, int64_t nnz, const int32_t 
       res->ortho = h->ortho;
       res->pi_iters_total = h->pi_total;
       res->gs_sweeps_total = h->gs_total;
+      res->refine_iters = h->refine_total;
     }
     res->status = out;
   }
@@ -457,8 +491,8 @@ fiedler_status ctx_reserve(BatchCtx &c, size_t dbytes, size_t hbytes) {
 }
 
 // device bytes one graph holds while its batch is in flight (admission)
-size_t item_footprint(int64_t n, int64_t nnz, size_t tsz, bool wf64) {
-  return r256(sizeof(State)) + r256(arena_estimate(n, nnz, tsz, wf64)) + r256(scratch_estimate(n, nnz, 1));
+size_t item_footprint(int64_t n, int64_t nnz, size_t tsz, bool wf64, const fiedler_options &o) {
+  return r256(sizeof(State)) + r256(arena_estimate(n, nnz, tsz, wf64, o)) + r256(scratch_estimate(n, nnz, 1, o));
 }
 
 // Lays out and queues one batched launch of c.items on c.stream (asynchronous).
@@ -473,8 +507,8 @@ fiedler_status batch_launch(fiedler_plan *p, BatchCtx &c, double arena_scale) {
   const int nslots = std::min(count, p->batch_slots[type][var]);
   size_t slot = 0, arenas = 0, in_b = 0, x_b = 0;
   for (auto &it : c.items) {
-    it.arena_b = r256((size_t)(arena_estimate(it.n, it.nnz, tsz, it.wf64) * arena_scale));
-    it.scratch_b = r256((size_t)(scratch_estimate(it.n, it.nnz, 1) * arena_scale));
+    it.arena_b = r256((size_t)(arena_estimate(it.n, it.nnz, tsz, it.wf64, p->opt) * arena_scale));
+    it.scratch_b = r256((size_t)(scratch_estimate(it.n, it.nnz, 1, p->opt) * arena_scale));
     slot = std::max(slot, it.scratch_b);
     arenas += it.arena_b;
     if (it.host_in) {
@@ -584,6 +618,7 @@ void batch_collect(BatchCtx &c) {
       r.ortho = h->ortho;
       r.pi_iters_total = h->pi_total;
       r.gs_sweeps_total = h->gs_total;
+      r.refine_iters = h->refine_total;
       if (it.user_x && !it.user_x_dev) memcpy(it.user_x, c.h_buf + c.h_x + it.x_off, 8 * (size_t)it.n);
     }
     r.x = it.user_x;
@@ -708,6 +743,7 @@ void ticket_result(const State *h, Ticket *t) {
     r.ortho = h->ortho;
     r.pi_iters_total = h->pi_total;
     r.gs_sweeps_total = h->gs_total;
+    r.refine_iters = h->refine_total;
   }
   r.x = t->x;
   r.x_on_device = 1;
@@ -778,7 +814,7 @@ void worker_main(fiedler_plan *p) {
           }
           if (ok && h->status == fz::ST_OK)
             p->arena_ratio = std::max(p->arena_ratio, (double)h->arena_off / (double)arena_estimate(
-                                                          t->n, t->nnz, tsz, t->w_dtype == FIEDLER_W_F64));
+                                                          t->n, t->nnz, tsz, t->w_dtype == FIEDLER_W_F64, p->opt));
           if (ok) ticket_result(h, t);
           else t->st = FIEDLER_ECUDA;
           if (ok)
@@ -813,8 +849,8 @@ void worker_main(fiedler_plan *p) {
         }
         // footprint with the learned arena factor (a rerun doubles t->scale)
         t->learn = p->arena_factor();
-        t->arena_b = r256((size_t)(arena_estimate(t->n, t->nnz, tsz, t->w_dtype == FIEDLER_W_F64) * t->scale * t->learn));
-        t->scratch_b = r256((size_t)(scratch_estimate(t->n, t->nnz, 1) * t->scale));
+        t->arena_b = r256((size_t)(arena_estimate(t->n, t->nnz, tsz, t->w_dtype == FIEDLER_W_F64, p->opt) * t->scale * t->learn));
+        t->scratch_b = r256((size_t)(scratch_estimate(t->n, t->nnz, 1, p->opt) * t->scale));
         t->footprint = r256(sizeof(State)) + t->arena_b + t->scratch_b;
         const bool empty = p->inflight_bytes == 0 && adm.empty();
         if (!empty && p->inflight_bytes + t->footprint > budget) break;  // wait for memory to free up
@@ -986,6 +1022,11 @@ void fiedler_options_default(fiedler_options *o) {
   o->max_batch = 1024;
   o->queue_budget_bytes = 0;
   o->batch_threads = 0;
+  o->refine = FIEDLER_REFINE_NONE;
+  o->refine_max_iters = 5000;
+  o->refine_tol = 1e-4;
+  o->lanczos_basis = 24;
+  o->hec_mode = FIEDLER_HEC_DOMINANT;
 }
 
 fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_stream, fiedler_plan **out) {
@@ -994,13 +1035,7 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
   fiedler_options o;
   if (opts) o = *opts;
   else fiedler_options_default(&o);
-  if ((o.precision != FIEDLER_FP64 && o.precision != FIEDLER_FP32_FP64RED) || o.coarse_max_n < 1 ||
-      o.max_levels < 1 || o.max_levels > fz::kMaxLevels || !(o.stall_ratio > 0.0 && o.stall_ratio <= 1.0) ||
-      o.gs_sweeps < 0 || o.pi_max_iters < 0 || o.pi_max_iters_coarsest < 0 || !(o.pi_cos_tol >= 0.0) ||
-      !(o.resid_tol >= 0.0) || (o.tie_rule != 0 && o.tie_rule != 1) || o.tail_max_n < 1 || o.tail_max_nnz < 1 ||
-      o.barrier_timeout_ms < 1 || o.max_batch < 1 ||
-      (o.batch_threads != 0 && o.batch_threads != 512 && o.batch_threads != 256 && o.batch_threads != 128))
-    return FIEDLER_EINVAL;
+  if (!fz::options_valid(o)) return FIEDLER_EINVAL;
   fiedler_plan *p = new (std::nothrow) fiedler_plan();
   if (!p) return FIEDLER_ENOMEM;
   p->opt = o;
@@ -1139,7 +1174,8 @@ fiedler_status fiedler_batch_submit(fiedler_plan *p, const fiedler_graph *g, uin
     free_ticket(p, t);
     return busy ? FIEDLER_EAGAIN : map_cuda(e);
   }
-  t->footprint = item_footprint(g->n, g->nnz, p->opt.precision == FIEDLER_FP64 ? 8 : 4, g->w_dtype == FIEDLER_W_F64);
+  t->footprint = item_footprint(g->n, g->nnz, p->opt.precision == FIEDLER_FP64 ? 8 : 4, g->w_dtype == FIEDLER_W_F64,
+                                p->opt);
   t->t_submit = std::chrono::steady_clock::now();
   std::lock_guard<std::mutex> lk(p->q_mu);
   t->id = p->next_ticket++;
@@ -1200,7 +1236,7 @@ fiedler_status fiedler_plan_autotune(fiedler_plan *p, const fiedler_graph *graph
   size_t bytes = 0;
   while (total < want) {
     const fiedler_graph &g = graphs[total % count];
-    const size_t f = item_footprint(g.n, g.nnz, tsz, g.w_dtype == FIEDLER_W_F64);
+    const size_t f = item_footprint(g.n, g.nnz, tsz, g.w_dtype == FIEDLER_W_F64, p->opt);
     if (total > 0 && bytes + f > budget) break;
     bytes += f;
     total++;
@@ -1415,6 +1451,7 @@ fiedler_status fiedler_plan_level_info(const fiedler_plan *p, int l, fiedler_lev
   info->color_rounds = L.color_rounds;
   info->gs_sweeps = L.gs_sweeps;
   info->pi_iters = L.pi_iters;
+  info->refine_iters = L.refine_iters;
   info->sigma = L.sigma;
   info->last_cos = L.last_cos;
   for (int i = 0; i < 16; i++) info->phase_ms[i] = i < fz::PH_COUNT ? (float)(p->h_state->level_ns[l][i] * 1e-6) : 0.f;

@@ -99,6 +99,200 @@ FZD void best_set(Best &b, uint64_t wk, int u, int v) {
 }
 
 // ---------------------------------------------------------------------------
+// Rayleigh-Ritz step of the LOBPCG refinement (one thread, FP64).  G and H are
+// the Gram matrix S^T S and the projection S^T L S of the basis S = [x, w, p]
+// (row-major 3 x 3).  The basis is scaled to unit columns, w and then p are
+// dropped when their Cholesky pivot of the scaled Gram matrix falls below
+// kRrPivot (nearly dependent directions), the k x k problem R^-1 H R^-T u =
+// theta u (G = R R^T) is solved by cyclic Jacobi rotations, and the smallest
+// Ritz value is returned with its coefficients c in the unscaled basis (0 for
+// dropped or unused vectors).  Returns a negative value if x alone is left
+// and no step is possible.
+constexpr double kRrPivot = 1e-10;
+
+FZD double rr3(const double *G, const double *H, bool use_w, bool use_p, double *c) {
+  int act[3], k;
+  double D[3], R[3][3], M[3][3], Vv[3][3];
+  for (;;) {
+    k = 0;
+    act[k++] = 0;
+    if (use_w) act[k++] = 1;
+    if (use_p) act[k++] = 2;
+    for (int i = 0; i < k; i++) D[i] = 1.0 / sqrt(G[act[i] * 3 + act[i]]);
+    int bad = -1;
+    for (int i = 0; i < k && bad < 0; i++) {
+      for (int j = 0; j <= i; j++) {
+        double sum = G[act[i] * 3 + act[j]] * D[i] * D[j];
+        for (int m = 0; m < j; m++) sum -= R[i][m] * R[j][m];
+        if (i == j) {
+          if (!(sum > kRrPivot)) {
+            bad = i;
+            break;
+          }
+          R[i][i] = sqrt(sum);
+        } else {
+          R[i][j] = sum / R[j][j];
+        }
+      }
+    }
+    if (bad < 0) break;
+    if (bad == 0) return -1.0;
+    if (act[bad] == 2) use_p = false;
+    else use_w = false;
+  }
+  if (k == 1) return -1.0;
+  // Y = R^-1 Hs (forward substitution, column by column), M = R^-1 Y^T
+  double Y[3][3];
+  for (int col = 0; col < k; col++)
+    for (int i = 0; i < k; i++) {
+      double sum = H[act[i] * 3 + act[col]] * D[i] * D[col];
+      for (int m = 0; m < i; m++) sum -= R[i][m] * Y[m][col];
+      Y[i][col] = sum / R[i][i];
+    }
+  for (int col = 0; col < k; col++)
+    for (int i = 0; i < k; i++) {
+      double sum = Y[col][i];
+      for (int m = 0; m < i; m++) sum -= R[i][m] * M[m][col];
+      M[i][col] = sum / R[i][i];
+    }
+  for (int i = 0; i < k; i++)
+    for (int j = 0; j < i; j++) M[i][j] = M[j][i] = 0.5 * (M[i][j] + M[j][i]);
+  for (int i = 0; i < k; i++)
+    for (int j = 0; j < k; j++) Vv[i][j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 50; sweep++) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < k; i++)
+      for (int j = 0; j < k; j++) {
+        tot += M[i][j] * M[i][j];
+        if (i != j) off += M[i][j] * M[i][j];
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int a = 0; a < k - 1; a++)
+      for (int b = a + 1; b < k; b++) {
+        if (M[a][b] == 0.0) continue;
+        const double th = (M[b][b] - M[a][a]) / (2.0 * M[a][b]);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int m = 0; m < k; m++) {  // columns a, b
+          const double ma = M[m][a], mb = M[m][b];
+          M[m][a] = cs * ma - sn * mb;
+          M[m][b] = sn * ma + cs * mb;
+        }
+        for (int m = 0; m < k; m++) {  // rows a, b
+          const double ma = M[a][m], mb = M[b][m];
+          M[a][m] = cs * ma - sn * mb;
+          M[b][m] = sn * ma + cs * mb;
+        }
+        for (int m = 0; m < k; m++) {
+          const double va = Vv[m][a], vb = Vv[m][b];
+          Vv[m][a] = cs * va - sn * vb;
+          Vv[m][b] = sn * va + cs * vb;
+        }
+      }
+  }
+  int mi = 0;
+  for (int i = 1; i < k; i++)
+    if (M[i][i] < M[mi][mi]) mi = i;
+  // y = R^-T u (back substitution), c = D y
+  double y[3];
+  for (int i = k - 1; i >= 0; i--) {
+    double sum = Vv[i][mi];
+    for (int m = i + 1; m < k; m++) sum -= R[m][i] * y[m];
+    y[i] = sum / R[i][i];
+  }
+  c[0] = c[1] = c[2] = 0.0;
+  for (int i = 0; i < k; i++) c[act[i]] = D[i] * y[i];
+  return M[mi][mi];
+}
+
+// Smallest eigenpair of the symmetric tridiagonal matrix with diagonal
+// al[0..k) and off-diagonal be[0..k-1) (one thread, FP64): the eigenvalue by
+// bisection on the Sturm count (number of eigenvalues below x = negative
+// pivots of the LDL^T factorisation of T - x I) inside the Gershgorin
+// interval, the eigenvector by two steps of inverse iteration (tridiagonal
+// elimination with partial pivoting) from the all-ones vector, normalised.
+FZD double tri_smallest(const double *al, const double *be, int k, double *s, double *work) {
+  double lo = al[0], hi = al[0];
+  for (int i = 0; i < k; i++) {
+    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < k ? fabs(be[i]) : 0.0);
+    lo = fmin(lo, al[i] - r);
+    hi = fmax(hi, al[i] + r);
+  }
+  const double scale = fmax(fabs(lo), fabs(hi)) + DBL_MIN;
+  for (int it = 0; it < 200 && hi - lo > 4.0 * DBL_EPSILON * scale; it++) {
+    const double x = 0.5 * (lo + hi);
+    int neg = 0;
+    double q = al[0] - x;
+    if (q == 0.0) q = -DBL_EPSILON * scale;
+    neg += q < 0.0;
+    for (int i = 1; i < k; i++) {
+      q = al[i] - x - be[i - 1] * be[i - 1] / q;
+      if (q == 0.0) q = -DBL_EPSILON * scale;
+      neg += q < 0.0;
+    }
+    if (neg >= 1) hi = x;
+    else lo = x;
+  }
+  const double th = 0.5 * (lo + hi);
+  // inverse iteration: solve (T - th I) y = s with partial pivoting; work holds
+  // the three diagonals of U and the multipliers (4k doubles)
+  double *u0 = work, *u1 = work + k, *u2 = work + 2 * k, *ml = work + 3 * k;
+  for (int i = 0; i < k; i++) s[i] = 1.0;
+  for (int rep = 0; rep < 2; rep++) {
+    // forward elimination with row interchanges: the pivot row carries entries
+    // in columns i, i+1, i+2 (c_d, c_e, c_f) and its right-hand side
+    double rhs_prev = s[0];
+    double c_d = al[0] - th, c_e = k > 1 ? be[0] : 0.0, c_f = 0.0;
+    for (int i = 0; i < k - 1; i++) {
+      const double sub = be[i], nd = al[i + 1] - th, ne = i + 2 < k ? be[i + 1] : 0.0;
+      double rn = s[i + 1];
+      if (fabs(c_d) >= fabs(sub)) {  // no interchange
+        const double mlt = c_d != 0.0 ? sub / c_d : 0.0;
+        u0[i] = c_d;
+        u1[i] = c_e;
+        u2[i] = c_f;
+        ml[i] = mlt;
+        s[i] = rhs_prev;
+        c_d = nd - mlt * c_e;
+        c_e = ne - mlt * c_f;
+        c_f = 0.0;
+        rhs_prev = rn - mlt * rhs_prev;
+      } else {  // interchange rows i and i+1
+        const double mlt = c_d / sub;
+        u0[i] = sub;
+        u1[i] = nd;
+        u2[i] = ne;
+        ml[i] = mlt;
+        s[i] = rn;
+        const double od = c_e - mlt * nd, oe = c_f - mlt * ne;
+        c_d = od;
+        c_e = oe;
+        c_f = 0.0;
+        rhs_prev = rhs_prev - mlt * rn;
+      }
+    }
+    u0[k - 1] = c_d;
+    u1[k - 1] = 0.0;
+    u2[k - 1] = 0.0;
+    s[k - 1] = rhs_prev;
+    // back substitution (tiny pivots replaced: the solution grows along the eigenvector)
+    double nrm = 0.0;
+    for (int i = k - 1; i >= 0; i--) {
+      double v = s[i];
+      if (i + 1 < k) v -= u1[i] * s[i + 1];
+      if (i + 2 < k) v -= u2[i] * s[i + 2];
+      double piv = u0[i];
+      if (fabs(piv) < DBL_EPSILON * scale) piv = piv < 0.0 ? -DBL_EPSILON * scale : DBL_EPSILON * scale;
+      s[i] = v / piv;
+    }
+    for (int i = 0; i < k; i++) nrm += s[i] * s[i];
+    nrm = 1.0 / sqrt(nrm);
+    for (int i = 0; i < k; i++) s[i] *= nrm;
+  }
+  return th;
+}
+
+// ---------------------------------------------------------------------------
 // shared storage: a static __shared__ declared in a function is one allocation
 // per kernel
 constexpr int kShSort = 2048;  // u64 words of the raw buffer (16 KB); also kWarpSeg per warp
@@ -488,7 +682,7 @@ struct Eng {
   unsigned ngen;    // grid barriers passed in this launch (same in every block)
   int cur_level;    // level being worked on (profile)
   // control flow, identical in every thread
-  int nlevels, setup_done, coarsest, coarsest_solved, solved, finalized;
+  int nlevels, setup_done, coarsest, coarsest_solved, solved, finalized, refined;
 
   // ---- infrastructure ------------------------------------------------------
   FZD void init(State *s) {
@@ -509,6 +703,7 @@ struct Eng {
     coarsest_solved = S->coarsest_solved;
     solved = S->solved;
     finalized = S->finalized;
+    refined = S->refined;
     t_last = 0;
     ngen = 0;
     cur_level = 0;
@@ -533,6 +728,7 @@ struct Eng {
       S->coarsest_solved = coarsest_solved;
       S->solved = solved;
       S->finalized = finalized;
+      S->refined = refined;
       if (status() == 0) S->arena_off = aoff;
     }
   }
@@ -734,6 +930,50 @@ struct Eng {
         if (threadIdx.x == 0)
 #pragma unroll
           for (int k = 0; k < K; k++) sh[k] = a[k];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < K; k++) v[k] = sh[k];
+      __syncthreads();
+      rb ^= 1;
+    } else {
+      if (!__syncthreads_and(status() == 0)) return false;
+    }
+    return true;
+  }
+
+  // FP64 grid sum of K <= kDSum values (the Krylov refinement's Gram sums):
+  // warp xor trees, the block's warps in fixed order, then (grid form) the
+  // blocks' partials in fixed order; result in every thread
+  template <int K>
+  FZD bool grid_wsum(double (&v)[K]) {
+    static_assert(K >= 1 && K <= kDSum, "grid_wsum: K <= kDSum");
+    double *sh = reinterpret_cast<double *>(sh_raw());  // [warps][K], then the K totals
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_dsum<K>(v);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < K; k++) sh[w * K + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < K) {
+      double a = 0.0;
+      for (int q = 0; q < nw; q++) a += sh[q * K + threadIdx.x];
+      sh[32 * K + threadIdx.x] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = sh[32 * K + k];
+    __syncthreads();
+    if (GRID) {
+      double *part = S->dpart + (size_t)rb * kMaxBlocks * kDSum;
+      if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) part[bid * kDSum + k] = v[k];
+      if (!sync()) return false;
+      if (threadIdx.x < K) {
+        double a = 0.0;
+        for (int b = 0; b < nb; b++) a += part[b * kDSum + threadIdx.x];
+        sh[threadIdx.x] = a;
       }
       __syncthreads();
 #pragma unroll
@@ -1570,6 +1810,217 @@ struct Eng {
     return true;
   }
 
+  // ---- A2 + A3, Alg. 1 as printed (hec_mode PAPER) -------------------------
+  // The sequential greedy: vertices visited in ascending order of the keys
+  // (splitmix64(seed + l, v), v); an unaggregated vertex u takes m(u), its
+  // heaviest neighbour (lowest index on ties); it founds the aggregate
+  // {u, m(u)} if m(u) is unaggregated, else joins m(u)'s aggregate; a vertex
+  // without neighbours founds a singleton; aggregate ids count up in visit
+  // order.  Reproduced exactly by rounds: A(u) = "u is unaggregated at its
+  // turn" is false iff some earlier v with m(v) = u has A(v) (decided once
+  // every such v is decided; the earliest undecided vertex is always
+  // decidable); first(u) = the earliest v with A(v) and m(v) = u took u (if u
+  // was not earlier than it) or joined it; u with A(u) founds iff m(u) < 0 or
+  // (u precedes m(u) and first(m(u)) = u), else joins m(u); an u without A(u)
+  // belongs to first(u)'s aggregate; joins are followed by pointer jumping
+  // (chains of m end in a founder: m has no cycles longer than two), and the
+  // founders are numbered in visit order by a bucket sort of their keys.
+  FZD bool hec_paper(int l, int &nc_out, GalerkinScratch &G) {
+    cur_level = l;
+    Level *L = &S->lv[l];
+    const int n = L->n;
+    const int *rp = L->rowptr, *ci = L->col;
+    const W wl = wof(L);
+    const uint64_t seed = S->opt.seed + (uint64_t)l;
+    const double stall = S->opt.stall_ratio;
+    int *hm = (int *)salloc(4ull * n);
+    int *st = (int *)salloc(4ull * n);  // 0 undecided, 1 A(u), 2 not A(u)
+    unsigned long long *fk = (unsigned long long *)salloc(8ull * n);
+    int *fv = (int *)salloc(4ull * n);
+    int *lab = (int *)salloc(4ull * n);
+    int *fid = (int *)salloc(4ull * n);
+    if (!hm || !st || !fk || !fv || !lab || !fid) return false;
+    auto key = [&](int v) { return sm64(seed, (uint64_t)(uint32_t)v); };
+    auto before = [&](int a, uint64_t ka, int b, uint64_t kb) { return ka < kb || (ka == kb && a < b); };
+    // m(v): heaviest neighbour, lowest index among equal weights (columns ascend)
+    for (int v = tid; v < n; v += nthr) {
+      int m = -1;
+      uint64_t bk = 0;
+      for (int e = rp[v]; e < rp[v + 1]; e++) {
+        const uint64_t wk = wl.key(e);
+        if (m < 0 || wk > bk) {
+          bk = wk;
+          m = ci[e];
+        }
+      }
+      hm[v] = m;
+      st[v] = 0;
+      fk[v] = ~0ull;
+      fv[v] = INT_MAX;
+    }
+    if (!sync_p()) return false;
+    int rounds = 0;
+    for (;; rounds++) {
+      IRed red{0, 0, 0};
+      for (int u = tid; u < n; u += nthr) {
+        if (st[u] != 0) continue;
+        const uint64_t ku = key(u);
+        bool pend = false, killed = false;
+        for (int e = rp[u]; e < rp[u + 1]; e++) {
+          const int v = ci[e];
+          if (hm[v] != u || !before(v, key(v), u, ku)) continue;
+          const int sv = *(volatile int *)&st[v];
+          if (sv == 1) {
+            killed = true;
+            break;
+          }
+          if (sv == 0) pend = true;
+        }
+        if (killed) st[u] = 2;
+        else if (!pend) st[u] = 1;
+        else red.a++;
+      }
+      if (!grid_ired<true>(red)) return false;
+      if (red.a == 0) break;
+      if (rounds > n) {
+        fail(ST_EINVAL);
+        return false;
+      }
+    }
+    // first(m): the earliest vertex with A that points at m
+    for (int w = tid; w < n; w += nthr)
+      if (st[w] == 1 && hm[w] >= 0) atomicMin(&fk[hm[w]], (unsigned long long)key(w));
+    if (!sync_p()) return false;
+    for (int w = tid; w < n; w += nthr)
+      if (st[w] == 1 && hm[w] >= 0 && (unsigned long long)key(w) == fk[hm[w]]) atomicMin(&fv[hm[w]], w);
+    if (!sync_p()) return false;
+    // founders, and a label per vertex: founders themselves, joiners m(u),
+    // the others the founder that took them
+    IRed nf_red{0, 0, 0};
+    for (int u = tid; u < n; u += nthr) {
+      int lb;
+      bool founder = false;
+      if (st[u] == 1) {
+        const int m = hm[u];
+        founder = m < 0 || (before(u, key(u), m, key(m)) && fv[m] == u);
+        lb = founder ? u : m;
+      } else {
+        lb = fv[u];
+      }
+      lab[u] = lb;
+      fid[u] = founder ? 1 : 0;
+      nf_red.a += founder;
+    }
+    if (!grid_ired<true>(nf_red)) return false;
+    const long long nc = nf_red.a;
+    for (;;) {
+      IRed red{0, 0, 0};
+      for (int u = tid; u < n; u += nthr) {
+        const int a = lab[u], b = lab[a];
+        if (b != a) {
+          lab[u] = b;
+          red.a++;
+        }
+      }
+      if (!grid_ired<true>(red)) return false;
+      if (red.a == 0) break;
+    }
+    nc_out = -1;
+    if (lead()) {
+      L->mate = nullptr;
+      L->match_rounds = rounds;
+    }
+    if (nc < 2 || (double)nc > stall * (double)n) return sync_p();
+    // founders in visit order: buckets by the top kb bits of the key
+    int kb = 1;
+    while (kb < 30 && (1ll << kb) < nc) kb++;
+    const int B = 1 << kb;
+    int *bcnt = (int *)salloc(4ull * B);
+    int *bst = (int *)salloc(4ull * (B + 1));
+    int *slot = (int *)salloc(4ull * nc);
+    if (!bcnt || !bst || !slot) return false;
+    for (int b = tid; b < B; b += nthr) bcnt[b] = 0;
+    if (!sync_p()) return false;
+    for (int u = tid; u < n; u += nthr)
+      if (fid[u]) atomicAdd(&bcnt[(int)(key(u) >> (64 - kb))], 1);
+    if (!sync_p()) return false;
+    {
+      int lo, hi;
+      chunk(B, lo, hi);
+      IRed red{0, 0, 0};
+      for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) red.a += bcnt[b];
+      long long pre = 0;
+      if (!grid_ired<true>(red, &pre)) return false;
+      long long run = pre;
+      for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+        const int b = t0 + threadIdx.x;
+        const int c = b < hi ? bcnt[b] : 0;
+        int tot;
+        const int ex = block_scan(c, &tot);
+        if (b < hi) bst[b] = (int)(run + ex);
+        run += tot;
+      }
+      if (lead()) bst[B] = (int)nc;
+    }
+    for (int b = tid; b < B; b += nthr) bcnt[b] = 0;
+    if (!sync_p()) return false;
+    for (int u = tid; u < n; u += nthr)
+      if (fid[u]) {
+        const int b = (int)(key(u) >> (64 - kb));
+        slot[bst[b] + atomicAdd(&bcnt[b], 1)] = u;
+      }
+    if (!sync_p()) return false;
+    // each bucket in key order (insertion sort: buckets hold ~1 founder)
+    for (int b = tid; b < B; b += nthr) {
+      const int s0 = bst[b], s1 = bst[b + 1];
+      for (int i = s0 + 1; i < s1; i++) {
+        const int v = slot[i];
+        const uint64_t kv = key(v);
+        int j = i - 1;
+        while (j >= s0 && before(v, kv, slot[j], key(slot[j]))) {
+          slot[j + 1] = slot[j];
+          j--;
+        }
+        slot[j + 1] = v;
+      }
+    }
+    if (!sync_p()) return false;
+    for (int p = tid; p < nc; p += nthr) fid[slot[p]] = p;
+    if (!sync_p()) return false;
+    int *agg = (int *)aalloc(4ull * n);
+    G.cnt = (int *)salloc(4ull * nc);
+    G.fill = (int *)salloc(4ull * nc);
+    G.tcnt = (int *)salloc(4ull * nc);
+    G.aggptr = (int *)salloc(4ull * (nc + 1));
+    G.segptr = (int *)salloc(4ull * (nc + 1));
+    G.dcnt = (int *)salloc(4ull * nc);
+    G.members = (int *)salloc(4ull * n);
+    G.cc = (int *)salloc(4ull * n);
+    G.memoff = (int *)salloc(4ull * n);
+    if (!agg || !G.cnt || !G.fill || !G.tcnt || !G.aggptr || !G.segptr || !G.dcnt || !G.members || !G.cc ||
+        !G.memoff)
+      return false;
+    for (long long I = tid; I < nc; I += nthr) {
+      G.cnt[I] = 0;
+      G.fill[I] = 0;
+      G.tcnt[I] = 0;
+    }
+    if (!sync_p()) return false;
+    for (int u = tid; u < n; u += nthr) {
+      const int a = fid[lab[u]];
+      agg[u] = a;
+      atomicAdd(&G.cnt[a], 1);
+    }
+    if (lead()) {  // published before the barrier: the Galerkin phase reads it
+      L->agg = agg;
+      L->nc = (int)nc;
+    }
+    if (!sync_p()) return false;
+    FZ_MARK(PH_MATCH, (4.0 * (n + 1) + (4.0 + (L->w64 ? 8.0 : 4.0)) * L->nnz) * (2.0 + rounds) + 60.0 * n);
+    nc_out = (int)nc;
+    return true;
+  }
+
   // ---- A4: Galerkin coarse operator I L I^T ---------------------------------
   FZD bool galerkin(int l, int nc, GalerkinScratch &G) {
     cur_level = l;
@@ -2038,7 +2489,8 @@ struct Eng {
     double mu, sc;
     if (!deflate_scalars(acc, n, mu, sc)) return false;
     FZ_MARK(PH_COARSEST, 16.0 * n + 8.0 * L->nnz);
-    return smooth(J, S->opt.pi_max_iters_coarsest, mu, sc, PH_COARSEST);
+    // with a Krylov refinement the finest level's power iteration is replaced by it
+    return smooth(J, (J == 0 && S->opt.refine) ? 0 : S->opt.pi_max_iters_coarsest, mu, sc, PH_COARSEST);
   }
 
   // ---- A8: prolongation y^j = I^T y^{j+1} ----------------------------------
@@ -2071,7 +2523,7 @@ struct Eng {
     double mu, sc;
     if (!deflate_scalars(acc, n, mu, sc)) return false;
     FZ_MARK(PH_PROLONG, 4.0 * n + (double)(sizeof(VF) + sizeof(VC)) * n);
-    return smooth(l, S->opt.pi_max_iters, mu, sc, PH_GS);
+    return smooth(l, (l == 0 && S->opt.refine) ? 0 : S->opt.pi_max_iters, mu, sc, PH_GS);
   }
 
   // ---- A9 + A10: Gauss-Seidel sweeps, then shifted power iteration ----------
@@ -2443,6 +2895,391 @@ struct Eng {
     return sync();
   }
 
+  // ---- finest-level Krylov refinement (Sec. 4's Krylov smoother) ----------
+  // Runs in place of the finest level's power iteration, after its
+  // Gauss-Seidel sweeps, until ||L x - theta x|| <= refine_tol theta ||x||.
+  FZD bool refine() {
+    cur_level = 0;
+    const int n = S->lv[0].n, nnz = S->lv[0].nnz;
+    if (GRID && vdbl(n, nnz) && sizeof(T) != 8) {  // see smooth()
+      fail(ST_ENOTSUP);
+      return false;
+    }
+    if (S->opt.refine == 1) return (!GRID && vdbl(n, nnz)) ? lobpcg_v<double>() : lobpcg_v<T>();
+    if (S->opt.refine == 2) return (!GRID && vdbl(n, nnz)) ? lanczos_v<double>() : lanczos_v<T>();
+    fail(ST_ENOTSUP);
+    return false;
+  }
+
+  // h[t] = sum_i Q_t[i] U[i] for t < k (k <= kMaxBasis + 1), FP64, in every
+  // thread's view of the shared array h: per warp by xor trees, the block's
+  // warps and (grid form) the blocks' partials in fixed order
+  template <class V>
+  FZD bool basis_dots(const V *Q, size_t ldq, const V *U, int n, int k, double *h) {
+    double *wp = reinterpret_cast<double *>(sh_raw());  // [warps][kMaxBasis + 1]
+    constexpr int LD = kMaxBasis + 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = 0; t < k; t++) {
+      const V *q = Q + (size_t)t * ldq;
+      double a = 0.0;
+      for (int i = tid; i < n; i += nthr) a += (double)q[i] * (double)U[i];
+      a = warp_sum(a);
+      if (lane == 0) wp[w * LD + t] = a;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+      double a = 0.0;
+      for (int q = 0; q < nw; q++) a += wp[q * LD + t];
+      h[t] = a;
+    }
+    __syncthreads();
+    if (GRID) {
+      double *part = S->dpart + (size_t)rb * kMaxBlocks * kDSum;
+      for (int t = threadIdx.x; t < k; t += blockDim.x) part[bid * kDSum + t] = h[t];
+      if (!sync()) return false;
+      for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        double a = 0.0;
+        for (int b = 0; b < nb; b++) a += part[b * kDSum + t];
+        h[t] = a;
+      }
+      __syncthreads();
+      rb ^= 1;
+    } else {
+      if (!__syncthreads_and(status() == 0)) return false;
+    }
+    return true;
+  }
+
+  // Lanczos with full reorthogonalisation (classical Gram-Schmidt, twice) on
+  // 1-perp, restarted from the smallest Ritz vector every lanczos_basis steps;
+  // the Ritz estimate beta_m |s_m| is tested at the end of each cycle.  Basis
+  // Q_0..Q_m (rows of n values), work vector U; the tridiagonal problem is
+  // solved by one thread.
+  template <class V>
+  FZD bool lanczos_v() {
+    Level *L = &S->lv[0];
+    const int n = L->n, nnz = L->nnz;
+    const int m = S->opt.lanczos_basis;
+    const size_t ld = ((size_t)n + 63) & ~(size_t)63;  // rows start on 256-byte boundaries
+    V *A = (V *)L->x;
+    V *Q = (V *)aalloc(sizeof(V) * ld * (size_t)(m + 1));
+    V *U = (V *)aalloc(sizeof(V) * (size_t)n);
+    if (!Q || !U) return false;
+    __shared__ double lz_al[kMaxBasis], lz_be[kMaxBasis], lz_h[kMaxBasis + 1], lz_s[kMaxBasis], lz_w[4 * kMaxBasis];
+    double *bc = sh_bc();
+    const double tol = S->opt.refine_tol;
+    const int kmax = S->opt.refine_max_iters;
+    const double inv_n = 1.0 / (double)n;
+    const double step_bytes = 4.0 * (n + 1) + (4.0 + sizeof(V)) * nnz + 2.0 * sizeof(V) * n;
+    // start: Q_0 = x (deflated, unit)
+    {
+      const V muT = (V)L->mu, sT = (V)L->s;
+      double acc[2] = {0.0, 0.0};
+      for (int i = tid; i < n; i += nthr) {
+        const V v = (A[i] - muT) * sT;
+        U[i] = v;
+        acc[0] += (double)v;
+        acc[1] += (double)v * (double)v;
+      }
+      if (!grid_wsum<2>(acc)) return false;
+      const double mq = acc[0] * inv_n, nq = 1.0 / sqrt(fmax(acc[1] - acc[0] * mq, DBL_MIN));
+      for (int i = tid; i < n; i += nthr) Q[i] = (V)(((double)U[i] - mq) * nq);
+      if (!sync()) return false;
+    }
+    int total = 0, capped = 0;
+    for (;;) {
+      int kk = 0;
+      for (int j = 0; j < m; j++) {
+        if (total >= kmax) break;
+        const V *qj = Q + (size_t)j * ld;
+        double acc[2] = {0.0, 0.0};
+        lap_rows<V>(L, qj, [&](int i, V lv, V dv) {
+          U[i] = lv;
+          acc[0] += (double)qj[i] * (double)lv;
+          acc[1] += (double)lv;
+        });
+        if (!grid_wsum<2>(acc)) return false;
+        total++;
+        const double al = acc[0], mu_u = acc[1] * inv_n, bprev = j > 0 ? lz_be[j - 1] : 0.0;
+        {
+          const V a = (V)al, mu = (V)mu_u, bp = (V)bprev;
+          const V *qp = j > 0 ? Q + (size_t)(j - 1) * ld : qj;
+          for (int i = tid; i < n; i += nthr) U[i] = U[i] - mu - a * qj[i] - bp * qp[i];
+        }
+        if (threadIdx.x == 0) lz_al[j] = al;
+        if (!sync()) return false;
+        for (int pass = 0; pass < 2; pass++) {
+          if (!basis_dots<V>(Q, ld, U, n, j + 1, lz_h)) return false;
+          for (int i = tid; i < n; i += nthr) {
+            double u = (double)U[i];
+            for (int t = 0; t <= j; t++) u -= lz_h[t] * (double)Q[(size_t)t * ld + i];
+            U[i] = (V)u;
+          }
+          if (!sync()) return false;
+        }
+        double nn[1] = {0.0};
+        for (int i = tid; i < n; i += nthr) nn[0] += (double)U[i] * (double)U[i];
+        if (!grid_wsum<1>(nn)) return false;
+        const double be = sqrt(nn[0]);
+        if (threadIdx.x == 0) lz_be[j] = be;
+        kk = j + 1;
+        FZ_MARK(PH_REFINE, step_bytes + (4.0 * (j + 1) + 4.0) * sizeof(V) * n);
+        if (!(be > 1e-12 * fabs(al))) break;  // invariant subspace
+        V *qn = Q + (size_t)(j + 1) * ld;
+        const V ib = (V)(1.0 / be);
+        for (int i = tid; i < n; i += nthr) qn[i] = U[i] * ib;
+        if (!sync()) return false;
+      }
+      if (kk == 0) {  // the cap was reached at a cycle boundary
+        capped = 1;
+        break;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double th = tri_smallest(lz_al, lz_be, kk, lz_s, lz_w);
+        bc[0] = th;
+        bc[1] = lz_be[kk - 1] * fabs(lz_s[kk - 1]);
+      }
+      __syncthreads();
+      const double theta = bc[0], est = bc[1];
+      __syncthreads();
+      // Ritz vector y = sum_t s_t Q_t into U, then deflated and normalised into Q_0
+      double acc[2] = {0.0, 0.0};
+      for (int i = tid; i < n; i += nthr) {
+        double y = 0.0;
+        for (int t = 0; t < kk; t++) y += lz_s[t] * (double)Q[(size_t)t * ld + i];
+        const V v = (V)y;
+        U[i] = v;
+        acc[0] += (double)v;
+        acc[1] += (double)v * (double)v;
+      }
+      if (!grid_wsum<2>(acc)) return false;
+      const double my = acc[0] * inv_n, ny = 1.0 / sqrt(fmax(acc[1] - acc[0] * my, DBL_MIN));
+      for (int i = tid; i < n; i += nthr) Q[i] = (V)(((double)U[i] - my) * ny);
+      if (!sync()) return false;
+      if (est <= tol * theta) break;
+      if (total >= kmax) {
+        capped = 1;
+        break;
+      }
+    }
+    if (lead()) {
+      L->x = Q;
+      L->y = U;
+      L->mu = 0.0;
+      L->s = 1.0;
+      L->refine_iters = total;
+      L->capped |= capped;
+    }
+    return sync();
+  }
+
+  // Row pass over level 0 in solve order: f(i, lv, d) with lv = sum_j w_ij
+  // (u_i - u_j) and d = sum_j w_ij in V; light rows one thread each, heavy rows
+  // a group of lanes each (f runs on the group's first lane).
+  template <class V, class F>
+  FZD void lap_rows(const Level *L, const V *u, F f) {
+    const int n = L->n;
+    const int *srp = L->srowptr, *scol = L->scol;
+    const V *sw = (const V *)L->sw;
+    const int nl = L->colstart[L->ncolors];
+    const int lane = threadIdx.x & 31, gw = tid >> 5, nwarp = nthr >> 5;
+    for (int i = tid; i < nl; i += nthr) {
+      const V ui = u[i];
+      V lv = (V)0, dv = (V)0;
+      const int e1 = srp[i + 1];
+      for (int e = srp[i]; e < e1; e++) {
+        const V wv = sw[e];
+        lv += wv * (ui - u[scol[e]]);
+        dv += wv;
+      }
+      f(i, lv, dv);
+    }
+    with_group<GRID>(heavy_group(srp, nl, n), [&](auto gs) {
+      constexpr int G = decltype(gs)::value, GW = 32 / G;
+      const int gl = lane & (G - 1), gi = lane / G;
+      for (int base = nl + gw * GW; base < n; base += nwarp * GW) {
+        const int i = base + gi;
+        V lv = (V)0, dv = (V)0;
+        if (i < n) {
+          const V ui = u[i];
+          group_row<G>(srp[i], srp[i + 1], scol, sw, [&](int j, V wv) {
+            lv += wv * (ui - u[j]);
+            dv += wv;
+          });
+        }
+        lv = group_sum<G>(lv);
+        dv = group_sum<G>(dv);
+        if (gl == 0 && i < n) f(i, lv, dv);
+      }
+    });
+  }
+
+  // LOBPCG (Knyazev 2001), one vector, on 1-perp with the preconditioner
+  // D^-1.  Iterate X, preconditioned residual W = D^-1 (L X - theta X), search
+  // direction P; the means of X, W and P are removed lazily (x = X - mu_x ...;
+  // L 1 = 0, so L-products need no correction).  The products L X and L P are
+  // computed afresh every iteration (a float recurrence for them drifts and
+  // lets the iteration diverge).  Per iteration: a matvec pass (L X, L P, the
+  // Rayleigh quotient and residual sums), a pass forming W, a matvec pass L W
+  // with the Gram sums of [x, w, p], one FP64 Rayleigh-Ritz step, an update
+  // pass.  Stops when ||L x - theta x|| <= refine_tol theta ||x||, when theta
+  // did not decrease in a step (each Rayleigh-Ritz step lowers it in exact
+  // arithmetic: this is the rounding floor of the value type; float iterates
+  // reach it near a residual of 1e-3 theta with lambda_2 exact to ~1e-8), or
+  // at refine_max_iters.
+  template <class V>
+  FZD bool lobpcg_v() {
+    Level *L = &S->lv[0];
+    const int n = L->n, nnz = L->nnz;
+    V *A = (V *)L->x;
+    V *X = (V *)aalloc(sizeof(V) * (size_t)n);
+    V *LX = (V *)aalloc(sizeof(V) * (size_t)n);
+    V *W = (V *)aalloc(sizeof(V) * (size_t)n);
+    V *LW = (V *)aalloc(sizeof(V) * (size_t)n);
+    V *P = (V *)aalloc(sizeof(V) * (size_t)n);
+    V *LP = (V *)aalloc(sizeof(V) * (size_t)n);
+    V *DI = (V *)aalloc(sizeof(V) * (size_t)n);
+    if (!X || !LX || !W || !LW || !P || !LP || !DI) return false;
+    const double tol = S->opt.refine_tol;
+    const int kmax = S->opt.refine_max_iters;
+    const double inv_n = 1.0 / (double)n;
+    const double it_bytes = 2.0 * (4.0 * (n + 1) + (4.0 + sizeof(V)) * nnz) + 16.0 * sizeof(V) * n;
+    double *bc = sh_bc();
+    {
+      const V muT = (V)L->mu, sT = (V)L->s;
+      for (int i = tid; i < n; i += nthr) X[i] = (A[i] - muT) * sT;
+      if (!sync()) return false;
+    }
+    double mux = 0.0, mup = 0.0, theta_prev = 0.0;
+    bool pvalid = false;
+    int iters = 0, capped = 0;
+    for (;;) {
+      // L X and L P afresh; sums for theta and the means (X's stored mean is
+      // the update's rounding only: it is measured here, and L 1 = 0)
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      lap_rows<V>(L, X, [&](int i, V lv, V dv) {
+        LX[i] = lv;
+        if (iters == 0) DI[i] = (V)1 / dv;
+        const double xv = (double)X[i], lx = (double)lv;
+        acc[0] += xv * xv;
+        acc[1] += xv * lx;
+        acc[2] += xv;
+      });
+      if (pvalid)
+        lap_rows<V>(L, P, [&](int i, V lv, V dv) {
+          LP[i] = lv;
+          acc[3] += (double)P[i];
+        });
+      if (!grid_wsum<4>(acc)) return false;
+      mux = acc[2] * inv_n;
+      mup = acc[3] * inv_n;
+      const double xx = acc[0] - acc[2] * mux, theta = acc[1] / xx;
+      // residual r = L x - theta x (its norm for the stop rule) and W = D^-1 r,
+      // whose mean mu_w is removed where W is read
+      double racc[2] = {0.0, 0.0};
+      {
+        const V mx = (V)mux, th = (V)theta;
+        for (int i = tid; i < n; i += nthr) {
+          const V r = LX[i] - th * (X[i] - mx);
+          const V wv = DI[i] * r;
+          W[i] = wv;
+          racc[0] += (double)r * (double)r;
+          racc[1] += (double)wv;
+        }
+      }
+      if (!grid_wsum<2>(racc)) return false;
+      const double muw = racc[1] * inv_n;
+      if (racc[0] <= tol * tol * theta * theta * xx) break;
+      if (iters > 0 && theta >= theta_prev) break;  // no descent: the rounding floor
+      if (iters >= kmax) {
+        capped = 1;
+        break;
+      }
+      theta_prev = theta;
+      // L W and the Gram sums of [x, w, p]
+      double g[12];
+#pragma unroll
+      for (int k = 0; k < 12; k++) g[k] = 0.0;
+      {
+        const V mx = (V)mux, mp = (V)mup, mw = (V)muw;
+        lap_rows<V>(L, W, [&](int i, V lv, V dv) {
+          LW[i] = lv;
+          const double xh = (double)(X[i] - mx), wh = (double)(W[i] - mw), lx = (double)LX[i];
+          const double lw = (double)lv;
+          g[0] += xh * xh;
+          g[1] += xh * wh;
+          g[3] += wh * wh;
+          g[6] += xh * lx;
+          g[7] += xh * lw;
+          g[9] += wh * lw;
+          if (pvalid) {
+            const double ph = (double)(P[i] - mp), lp = (double)LP[i];
+            g[2] += xh * ph;
+            g[4] += wh * ph;
+            g[5] += ph * ph;
+            g[8] += xh * lp;
+            g[10] += wh * lp;
+            g[11] += ph * lp;
+          }
+        });
+      }
+      if (!grid_wsum<12>(g)) return false;
+      iters++;
+      FZ_MARK(PH_REFINE, it_bytes);
+      if (threadIdx.x == 0) {
+        const double G[9] = {g[0], g[1], g[2], g[1], g[3], g[4], g[2], g[4], g[5]};
+        const double H[9] = {g[6], g[7], g[8], g[7], g[9], g[10], g[8], g[10], g[11]};
+        double c[3];
+        const double th = rr3(G, H, true, pvalid, c);
+        double nx = 0.0, np = 0.0;
+        if (th > 0.0)
+          for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+              nx += c[a] * G[a * 3 + b] * c[b];
+              if (a > 0 && b > 0) np += c[a] * G[a * 3 + b] * c[b];
+            }
+        const bool ok = th > 0.0 && nx > 0.0;
+        const double ix = ok ? 1.0 / sqrt(nx) : 0.0;
+        const double ip = (ok && np > 1e-300) ? 1.0 / sqrt(np) : 0.0;
+        bc[0] = ok ? 1.0 : 0.0;
+        bc[1] = c[0] * ix;
+        bc[2] = c[1] * ix;
+        bc[3] = c[2] * ix;
+        bc[4] = c[1] * ip;
+        bc[5] = c[2] * ip;
+        bc[6] = ip > 0.0 ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      const bool ok = bc[0] != 0.0;
+      const V a0 = (V)bc[1], a1 = (V)bc[2], a2 = (V)bc[3], b1 = (V)bc[4], b2 = (V)bc[5];
+      const bool pnext = bc[6] != 0.0;
+      __syncthreads();
+      if (!ok) break;  // no step left (w and p dependent on x): x is final
+      // x <- a0 x + a1 w + a2 p,  p <- b1 w + b2 p  (means removed)
+      {
+        const V mx = (V)mux, mp = (V)mup, mw = (V)muw;
+        for (int i = tid; i < n; i += nthr) {
+          const V xh = X[i] - mx, wh = W[i] - mw, ph = pvalid ? P[i] - mp : (V)0;
+          X[i] = a0 * xh + a1 * wh + a2 * ph;
+          if (pnext) P[i] = b1 * wh + b2 * ph;
+        }
+        mux = 0.0;
+        pvalid = pnext;
+        if (!sync()) return false;
+      }
+    }
+    if (lead()) {
+      L->x = X;
+      L->y = W;
+      L->mu = mux;
+      L->s = 1.0;
+      L->refine_iters = iters;
+      L->capped |= capped;
+    }
+    return sync();
+  }
+
   // ---- A11: Rayleigh quotient, residual, orthogonality, sign, output --------
   FZD bool finalize() {
     const int n = S->lv[0].n, nnz = S->lv[0].nnz;
@@ -2467,14 +3304,16 @@ struct Eng {
     // are taken in V (neighbouring values of a smooth vector are close, so
     // their difference is exact in V) and accumulated over rows in FP64, scaled
     // by s and s^2 at the end.
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    // the row sums (L x)_k / s are kept in y for the residual pass below
+    V *LXk = (V *)L->y;
+    double acc[3] = {0.0, 0.0, 0.0};
     IRed big{0, 0, LLONG_MIN};
-    auto row = [&](V xi, V lx, V num) {
+    auto row = [&](int k, V xi, V lx, V num) {
       const double xk = ((double)xi - mu) * s;
       acc[0] += xk * xk;
       acc[1] += xk;
       acc[2] += (double)num;
-      acc[3] += (double)lx * (double)lx;
+      LXk[k] = lx;
       big.mx = max(big.mx, (long long)__double_as_longlong(fabs(xk)));
     };
     const int nl = L->colstart[L->ncolors];  // light rows [0, nl), heavy rows [nl, n)
@@ -2490,7 +3329,7 @@ struct Eng {
           lx += wd;
           num += wd * dl;
         }
-        row(xi, lx, num);
+        row(k, xi, lx, num);
       }
       with_group<GRID>(heavy_group(srp, nl, n), [&](auto gs) {  // heavy rows: a group of lanes each
         constexpr int G = decltype(gs)::value, GW = 32 / G;
@@ -2509,13 +3348,23 @@ struct Eng {
           }
           lx = group_sum<G>(lx);
           num = group_sum<G>(num);
-          if (gl == 0 && k < n) row(xi, lx, num);
+          if (gl == 0 && k < n) row(k, xi, lx, num);
         }
       });
     }
-    if (!grid_dsum<4>(acc)) return false;
+    if (!grid_dsum<3>(acc)) return false;
     acc[2] *= s * s;
-    acc[3] *= s * s;
+    // residual ||L x - lambda x|| / ||x|| from its own sum of squares (a
+    // difference of ||L x||^2 and lambda^2 ||x||^2 would cancel when the
+    // residual is small)
+    const double lam0 = acc[2] / (2.0 * acc[0]);
+    double rac[1] = {0.0};
+    for (int k = tid; k < n; k += nthr) {
+      const double xk = ((double)A[k] - mu) * s;
+      const double rk = s * (double)LXk[k] - lam0 * xk;
+      rac[0] += rk * rk;
+    }
+    if (!grid_dsum<1>(rac)) return false;
     if (!grid_ired(big)) return false;
     // lowest original index among the entries of largest |x|
     const long long bits = big.mx;
@@ -2527,18 +3376,19 @@ struct Eng {
     if (!grid_ired(low)) return false;
     const int imax = (int)(-low.mx);
     const double xx = acc[0];
-    const double lam = acc[2] / (2.0 * xx);
-    const double r2 = acc[3] / xx - lam * lam;
+    const double lam = lam0;
+    const double r2 = rac[0] / xx;
     const double xbig = ((double)A[iperm[imax]] - mu) * s;
     const double sign = xbig < 0.0 ? -1.0 : 1.0;
     const double inv = sign / sqrt(xx);
     double *out = S->xout;
     if (out)
       for (int k = tid; k < n; k += nthr) out[perm[k]] = ((double)A[k] - mu) * s * inv;
-    int ptot = 0, gtot = 0, cap = 0;
+    int ptot = 0, gtot = 0, rtot = 0, cap = 0;
     for (int l = 0; l < nlevels; l++) {
       ptot += S->lv[l].pi_iters;
       gtot += S->lv[l].gs_sweeps;
+      rtot += S->lv[l].refine_iters;
       cap |= S->lv[l].capped;
     }
     if (lead()) {
@@ -2547,10 +3397,11 @@ struct Eng {
       S->ortho = fabs(acc[1]) / (sqrt((double)n) * sqrt(xx));
       S->pi_total = ptot;
       S->gs_total = gtot;
+      S->refine_total = rtot;
       S->capped = cap;
     }
     if (!sync()) return false;
-    FZ_MARK(PH_FINAL, 4.0 * (n + 1) + (4.0 + sizeof(V)) * nnz + (2.0 * sizeof(V) + 8.0 + 8.0) * n);
+    FZ_MARK(PH_FINAL, 4.0 * (n + 1) + (4.0 + sizeof(V)) * nnz + (4.0 * sizeof(V) + 8.0 + 8.0) * n);
     return true;
   }
 
@@ -2575,8 +3426,12 @@ struct Eng {
         GalerkinScratch G;
         int nc = -1;
         if (!last) {
-          if (!match(l)) return false;
-          if (!aggregate(l, nc, G)) return false;
+          if (S->opt.hec_mode == 1) {
+            if (!hec_paper(l, nc, G)) return false;
+          } else {
+            if (!match(l)) return false;
+            if (!aggregate(l, nc, G)) return false;
+          }
           last = nc < 0;
           if (!last && !galerkin(l, nc, G)) return false;
         }
@@ -2606,6 +3461,11 @@ struct Eng {
       if (!elig(S->lv[l].n, S->lv[l].nnz)) return true;
       if (!prolong(l)) return false;
       solved = l;
+      persist();
+    }
+    if (S->opt.refine && !refined) {
+      if (!refine()) return false;
+      refined = 1;
       persist();
     }
     if (!finalized) {

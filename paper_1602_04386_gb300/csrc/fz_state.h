@@ -16,10 +16,11 @@ constexpr int kGridThreads = 512;  // grid-wide kernel block size
 // engine, smoothed by one warp, values in FP64 in both forms
 constexpr int kTinyN = 256;
 constexpr int kTinyNnz = 4096;
+constexpr int kMaxBasis = 64;      // Lanczos basis vectors per restart cycle, at most
 
 enum Phase {
   PH_INGEST = 0, PH_COLOR, PH_REORDER, PH_MATCH, PH_AGG, PH_GALERKIN,
-  PH_COARSEST, PH_PROLONG, PH_GS, PH_PI, PH_FINAL, PH_COUNT
+  PH_COARSEST, PH_PROLONG, PH_GS, PH_PI, PH_FINAL, PH_REFINE, PH_COUNT
 };
 
 // internal status codes; the host maps them to fiedler_status
@@ -40,6 +41,11 @@ struct Opts {
   int tail_max_n;
   int tail_max_nnz;
   int fault_inject;
+  int refine;                // 0: paper (power iteration); 1: LOBPCG; 2: Lanczos (finest level)
+  int refine_max_iters;
+  int lanczos_basis;
+  int hec_mode;              // 0: locally dominant matching; 1: Alg. 1's random-order greedy
+  double refine_tol;
   double stall_ratio;
   double pi_cos_tol;
   double resid_tol;
@@ -72,10 +78,11 @@ struct Level {
   double mu, s;
   // counters
   int match_rounds, color_rounds, gs_sweeps, pi_iters, capped;
+  int refine_iters;
   double last_cos;
 };
 
-constexpr int kDSum = 6;   // doubles per block partial of a floating-point grid sum
+constexpr int kDSum = 72;  // doubles per block partial of a floating-point grid sum (>= kMaxBasis + 1)
 
 struct IRed {              // per-block partials of an integer grid reduction
   long long a, b;          // sums (prefix over lower blocks available for both)
@@ -91,6 +98,7 @@ struct State {
   int coarsest_solved;
   int solved;              // lowest level index whose vector is final
   int finalized;
+  int refined;             // the finest level's Krylov refinement is done
   int capped;
   Opts opt;
   // input graph
@@ -113,7 +121,7 @@ struct State {
   int col_max;             // largest colour of the level being coloured
   // results
   double lambda, residual, ortho;
-  int pi_total, gs_total;
+  int pi_total, gs_total, refine_total, pad3;
   // grid barrier: one word whose top bit flips when every block has arrived;
   // failword = (barriers passed by the failing block << 32) | status code
   unsigned bar_word;

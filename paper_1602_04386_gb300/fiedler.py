@@ -37,6 +37,11 @@ FIEDLER_TIE_HASHED = 0
 FIEDLER_TIE_INDEX = 1
 FIEDLER_W_F32 = 0
 FIEDLER_W_F64 = 1
+FIEDLER_REFINE_NONE = 0
+FIEDLER_REFINE_LOBPCG = 1
+FIEDLER_REFINE_LANCZOS = 2
+FIEDLER_HEC_DOMINANT = 0
+FIEDLER_HEC_PAPER = 1
 
 #: exported symbols declared in include/fiedler.h
 SYMBOLS = (
@@ -70,6 +75,11 @@ class fiedler_options(C.Structure):
         ("max_batch", C.c_int),
         ("queue_budget_bytes", C.c_size_t),
         ("batch_threads", C.c_int),
+        ("refine", C.c_int),
+        ("refine_max_iters", C.c_int),
+        ("refine_tol", C.c_double),
+        ("lanczos_basis", C.c_int),
+        ("hec_mode", C.c_int),
     ]
 
 
@@ -99,6 +109,7 @@ class fiedler_result(C.Structure):
         ("ms", C.c_float),
         ("bad_index", C.c_longlong),
         ("status", C.c_int),
+        ("refine_iters", C.c_int),
     ]
 
 
@@ -115,6 +126,7 @@ class fiedler_level_info(C.Structure):
         ("sigma", C.c_double),
         ("last_cos", C.c_double),
         ("phase_ms", C.c_float * 16),
+        ("refine_iters", C.c_int),
     ]
 
 
@@ -326,6 +338,7 @@ class Result:
         self.gs_sweeps_total = r.gs_sweeps_total
         self.ms = r.ms
         self.bad_index = r.bad_index
+        self.refine_iters = r.refine_iters
         self.x = x
 
     def __repr__(self):

@@ -40,6 +40,11 @@ def check_against_oracle(g, precision, lam_tol, tail=4096, tail_nnz=32768):
             if l + 1 < p.num_levels:
                 assert np.array_equal(a["agg"], b.agg), l
     assert abs(r.lambda2 - ref.lam) <= lam_tol * abs(ref.lam), (r.lambda2, ref.lam)
+    # reported residual and orthogonality against the oracle's (same counts)
+    rt, at = (1e-6, 1e-12) if precision == FP64 else (1e-2, 1e-6)
+    sigma = ref.level(0).sigma
+    assert abs(r.residual - ref.residual) <= rt * ref.residual + at * sigma, (r.residual, ref.residual)
+    assert abs(r.ortho - ref.ortho) <= (1e-12 if precision == FP64 else 1e-9)
     return r
 
 

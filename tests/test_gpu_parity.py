@@ -6,7 +6,11 @@ Bars (written in each test):
   * FP64 form: lambda_2 within 1e-10 relative of the oracle run with the same
     per-level power-iteration counts, vector within 1e-8;
   * FP32 form (float values and matvec, double reductions): lambda_2 within
-    1e-5 relative of the FP64 oracle with the same counts;
+    1e-5 relative of the FP64 oracle with the same counts, vector angle
+    1 - |cos| <= 1e-6 to the oracle's vector;
+  * residual ||Lx - lambda x|| / ||x|| and orthogonality |1^T x| / (sqrt(n)||x||)
+    against the oracle's: FP64 1e-6 relative (+ 1e-12 sigma), FP32 1e-2
+    relative (+ 1e-6 sigma: float rounding of Lx);
   * tight convergence: angle 1 - |cos| <= 1e-6 to the closed-form vector.
 """
 import numpy as np
@@ -55,6 +59,14 @@ def assert_hierarchy_equal(p, ref):
             assert a["info"].nc == b.nc
 
 
+def assert_residual_ortho(r, ref, precision, sigma):
+    """The GPU's reported residual and orthogonality against the oracle's (same
+    iteration counts): FP64 to rounding, FP32 up to the float rounding of L x."""
+    rt, at = (1e-6, 1e-12) if precision == FP64 else (1e-2, 1e-6)
+    assert abs(r.residual - ref.residual) <= rt * ref.residual + at * sigma, (r.residual, ref.residual)
+    assert abs(r.ortho - ref.ortho) <= (1e-12 if precision == FP64 else 1e-9), (r.ortho, ref.ortho)
+
+
 def compare(g, precision, lam_tol, x_tol=None, **kw):
     with plan(precision=precision, **kw) as p:
         r = p.solve(g)
@@ -71,6 +83,9 @@ def compare(g, precision, lam_tol, x_tol=None, **kw):
         x = ref.x(g.n)
         if x_tol is not None:
             assert np.abs(r.x - x).max() <= x_tol
+        assert_residual_ortho(r, ref, precision, p.level_info(0).sigma)
+        if precision == FP32:
+            assert 1 - abs(r.x @ x) <= 1e-6
         # FP64 form: the oracle's own stop rule gives the same counts unless a cos
         # test sat on the threshold.  (The FP32 form takes its stop decisions on
         # float iterates, so its counts may differ; the comparison above replays

@@ -38,11 +38,19 @@ def _noalloc(g, precision, stream):
     return st, r, x.cpu().numpy(), keep
 
 
+GRAPHS = {
+    "grid64x48": lambda: inputs.grid(64, 48, "unit"),
+    "grid150x101w": lambda: inputs.grid(150, 101, "uniform", seed=7),
+    "grid15x11w": lambda: inputs.grid(15, 11, "uniform", seed=2),  # n <= 256: the tiny-level path
+    "knn6000": lambda: inputs.knn_mixture(6000, seed=4),
+    "rmat13": lambda: inputs.rmat(13, seed=6),  # skewed degrees, near the array's size limit
+}
+
+
 @pytest.mark.parametrize("precision", [fiedler.FIEDLER_FP64, fiedler.FIEDLER_FP32_FP64RED])
-@pytest.mark.parametrize("graph", ["grid64x48", "grid150x101w"])
+@pytest.mark.parametrize("graph", list(GRAPHS))
 def test_noalloc_matches_plan_solve_twice(precision, graph):
-    g = {"grid64x48": lambda: inputs.grid(64, 48, "unit"),
-         "grid150x101w": lambda: inputs.grid(150, 101, "uniform", seed=7)}[graph]()
+    g = GRAPHS[graph]()
     lam_tol, x_tol = TOL[precision]
     with fiedler.Plan(precision=precision, tail_max_n=1 << 30, tail_max_nnz=1 << 30) as p:
         ref = p.solve(g)
@@ -56,12 +64,41 @@ def test_noalloc_matches_plan_solve_twice(precision, graph):
         assert r.levels == ref.levels
 
 
+def test_noalloc_allocates_no_device_memory():
+    """After a first call (which looks up the array's address), further calls
+    leave the device's free memory unchanged."""
+    g = inputs.grid(90, 70, "uniform", seed=5)
+    stream = torch.cuda.current_stream().cuda_stream
+    gs, keep = fiedler.device_graph(g)
+    x = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    r = fiedler.fiedler_result()
+    assert fiedler.fiedler_solve_noalloc(None, gs, x.data_ptr(), stream, r) == fiedler.FIEDLER_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert fiedler.fiedler_solve_noalloc(None, gs, x.data_ptr(), stream, r) == fiedler.FIEDLER_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_noalloc_refuses_too_large_and_host_inputs():
     big = inputs.grid(1024, 768, "uniform", seed=1)
     gs, keep = fiedler.device_graph(big)
     r = fiedler.fiedler_result()
+    r.status = 12345
     st = fiedler.fiedler_solve_noalloc(None, gs, None, None, r)
-    assert st == fiedler.FIEDLER_ENOTSUP
+    assert st == fiedler.FIEDLER_ENOTSUP and r.status == st and r.bad_index == -1
     small = inputs.grid(20, 10)
     hs, hkeep = fiedler.host_graph(small)
+    r.status = 12345
     assert fiedler.fiedler_solve_noalloc(None, hs, None, None, r) == fiedler.FIEDLER_EINVAL
+    assert r.status == fiedler.FIEDLER_EINVAL
+    # the options are checked as fiedler_plan_create checks them
+    sg, skeep = fiedler.device_graph(small)
+    for field, bad in (("tie_rule", 7), ("pi_cos_tol", float("nan")), ("resid_tol", -1.0), ("refine", 9)):
+        o = fiedler.fiedler_options_default()
+        setattr(o, field, bad)
+        r.status = 12345
+        assert fiedler.fiedler_solve_noalloc(o, sg, None, None, r) == fiedler.FIEDLER_EINVAL, field
+        assert r.status == fiedler.FIEDLER_EINVAL
