@@ -62,6 +62,7 @@ class Opts(C.Structure):
         ("refine_tol", C.c_double),
         ("lanczos_basis", C.c_int),
         ("refine_forced", C.c_int),
+        ("refine_precond", C.c_int),
     ]
 
 
@@ -69,6 +70,7 @@ HEC_HANDSHAKE, HEC_GREEDY, HEC_PAPER = 0, 1, 2
 TIE_HASHED, TIE_INDEX = 0, 1
 GS_LEX, GS_COLORED = 0, 1
 REFINE_NONE, REFINE_LOBPCG, REFINE_LANCZOS = 0, 1, 2
+PRECOND_DEGREE, PRECOND_VCYCLE = 0, 1
 
 
 def lib():
@@ -106,6 +108,7 @@ def lib():
             L.oracle_jacobi_eig.restype = C.c_int
             L.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
             L.oracle_splitmix64.restype = C.c_uint64
+            L.oracle_vcycle.argtypes = [C.c_void_p, dp, dp]
             L.oracle_uniform01.argtypes = [C.c_uint64, C.c_uint64]
             L.oracle_uniform01.restype = C.c_double
             _lib = L
@@ -207,6 +210,15 @@ class Run:
     @property
     def pi_iters(self):
         return [self.level(l).pi_iters for l in range(self.num_levels)]
+
+    def vcycle(self, b):
+        """One V-cycle of the run's hierarchy applied to b (level-0 numbering)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        e = np.zeros_like(b)
+        st = lib().oracle_vcycle(self._h, _dp(b), _dp(e))
+        if st != OK:
+            raise RuntimeError(f"oracle_vcycle status {st}")
+        return e
 
     @property
     def refine_iters(self):

@@ -80,6 +80,14 @@
  *       happens at the rounding floor of the arithmetic (in float the residual
  *       stalls near 1e-3 theta on graphs of small lambda_2 while lambda_2
  *       itself is already exact to ~1e-8).
+ *   R13 LOBPCG's preconditioner (refine_precond; not in the paper): D^-1, or
+ *       one V-cycle of the cascade's own hierarchy on L e = r: on level l, one
+ *       forward Gauss-Seidel sweep from e = 0 (colour classes ascending), the
+ *       residual r - L e summed over each aggregate (members in ascending
+ *       index) as the next level's right-hand side, the next level's
+ *       correction added to every member, one backward sweep (classes
+ *       descending); on the coarsest level 20 forward sweeps from e = 0 and
+ *       the mean removed.
  */
 #include <math.h>
 #include <stdint.h>
@@ -144,6 +152,7 @@ typedef struct {
   double refine_tol;         /* stop: ||L x - theta x|| <= refine_tol * theta * ||x|| */
   int lanczos_basis;         /* Lanczos steps per restart cycle */
   int refine_forced;         /* >= 0: run exactly this many matvecs (replay); -1: stop rule */
+  int refine_precond;        /* LOBPCG preconditioner: 0 D^-1, 1 one V-cycle of the hierarchy (R13) */
 } oracle_opts;
 
 typedef struct {
@@ -232,6 +241,7 @@ void oracle_default_opts(oracle_opts *o) {
   o->refine_tol = 1e-4;
   o->lanczos_basis = 24;
   o->refine_forced = -1;
+  o->refine_precond = 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -774,10 +784,16 @@ int oracle_jacobi_eig(int n, double *A, double *evals, double *V, int max_sweeps
 /* ------------------------------------------------------------------------ */
 /* Level smoothing: Gauss-Seidel sweeps (R5) then power iteration (R6). */
 
+/* colour classes ascending, ascending index within a class (lexicographic
+ * when the level has no colouring) */
 static int *colour_order(const orc_level *lv) {
   int n = lv->L.n;
   int *order = (int *)malloc(sizeof(int) * (size_t)n);
   if (!order) return NULL;
+  if (!lv->color) {
+    for (int i = 0; i < n; i++) order[i] = i;
+    return order;
+  }
   int t = 0;
   for (int c = 0; c < lv->ncolors; c++)
     for (int i = 0; i < n; i++)
@@ -904,9 +920,50 @@ static int rayleigh_ritz(int n, double *const *Sv, double *const *LS, int k, dou
   return m;
 }
 
-/* (1) LOBPCG with preconditioner D^-1 on 1-perp.  x: unit vector, orthogonal
- * to 1, replaced by the refined vector.  forced >= 0 runs that many steps. */
-static int refine_lobpcg(orc_level *lv, double *x, const oracle_opts *o) {
+/* One V-cycle (reading R13) for L_l e = b on levels l..J of the run's
+ * hierarchy; e is overwritten. */
+static int vcycle(const oracle_run *r, int l, const double *b, double *e) {
+  const orc_level *lv = &r->lv[l];
+  const orc_lap *L = &lv->L;
+  int n = L->n, J = r->nlevels - 1;
+  int *order = colour_order(lv);
+  if (!order) return ORC_ENOMEM;
+  for (int i = 0; i < n; i++) e[i] = 0.0;
+  if (l == J) {
+    for (int k = 0; k < 20; k++) gs_sweep(n, L->rowptr, L->col, L->w, L->d, b, e, order);
+    double mu = vsum(n, e) / (double)n;
+    for (int i = 0; i < n; i++) e[i] -= mu;
+    free(order);
+    return ORC_OK;
+  }
+  gs_sweep(n, L->rowptr, L->col, L->w, L->d, b, e, order);
+  int nc = lv->nc;
+  double *t = (double *)malloc(sizeof(double) * (size_t)n);
+  double *bc = (double *)calloc((size_t)nc, sizeof(double));
+  double *ec = (double *)malloc(sizeof(double) * (size_t)nc);
+  if (!t || !bc || !ec) { free(order); free(t); free(bc); free(ec); return ORC_ENOMEM; }
+  lap_apply(L, e, t);
+  for (int i = 0; i < n; i++) bc[lv->agg[i]] += b[i] - t[i];
+  int st = vcycle(r, l + 1, bc, ec);
+  if (st == ORC_OK) {
+    for (int i = 0; i < n; i++) e[i] += ec[lv->agg[i]];
+    for (int a = 0, z = n - 1; a < z; a++, z--) { int q = order[a]; order[a] = order[z]; order[z] = q; }
+    gs_sweep(n, L->rowptr, L->col, L->w, L->d, b, e, order);
+  }
+  free(order); free(t); free(bc); free(ec);
+  return st;
+}
+
+/* exported for the pins: e = V(b) on the hierarchy of a finished run */
+int oracle_vcycle(const oracle_run *r, const double *b, double *e) {
+  if (!r || r->nlevels < 1) return ORC_EINVAL;
+  return vcycle(r, 0, b, e);
+}
+
+/* (1) LOBPCG with preconditioner D^-1 or one V-cycle (R13) on 1-perp.  x:
+ * unit vector, orthogonal to 1, replaced by the refined vector.  forced >= 0
+ * runs that many steps. */
+static int refine_lobpcg(const oracle_run *run, orc_level *lv, double *x, const oracle_opts *o) {
   const orc_lap *L = &lv->L;
   int n = L->n;
   double *lx = (double *)malloc(sizeof(double) * (size_t)n);
@@ -934,7 +991,13 @@ static int refine_lobpcg(orc_level *lv, double *x, const oracle_opts *o) {
     if (forced >= 0 && k >= forced) break;
     if (forced < 0 && k >= o->refine_max_iters) { lv->capped = 1; break; }
     theta_prev = theta;
-    for (int i = 0; i < n; i++) w[i] /= L->d[i];
+    if (o->refine_precond == 1) {
+      memcpy(xn, w, sizeof(double) * (size_t)n);
+      int vst = vcycle(run, 0, xn, w);
+      if (vst != ORC_OK) { free(lx); free(w); free(lw); free(p); free(lp); free(xn); return vst; }
+    } else {
+      for (int i = 0; i < n; i++) w[i] /= L->d[i];
+    }
     double mw = vsum(n, w) / (double)n;
     for (int i = 0; i < n; i++) w[i] -= mw;
     lap_apply(L, w, lw);
@@ -1183,7 +1246,7 @@ int oracle_solve(oracle_run *r, int n, long long nnz, const int *rowptr, const i
   /* finest-level Krylov refinement (reading R12) */
   if (o->refine == 1 || o->refine == 2) {
     orc_level *l0 = &r->lv[0];
-    st = (o->refine == 1) ? refine_lobpcg(l0, l0->x, o) : refine_lanczos(l0, l0->x, o);
+    st = (o->refine == 1) ? refine_lobpcg(r, l0, l0->x, o) : refine_lanczos(l0, l0->x, o);
     if (st != ORC_OK) return st;
   }
   /* Rayleigh quotient on the finest level, residual, orthogonality, sign */

@@ -73,6 +73,12 @@ MUTANTS = [
      "sqrt(rr) <= o->refine_tol * sqrt(vdot(n, x, x))"),
     ("lobpcg_stall_rule_loose", "if (forced < 0 && k > 0 && theta >= theta_prev) break;",
      "if (forced < 0 && k > 0 && theta >= theta_prev * (1.0 - 1e-3)) break;"),
+    ("vcycle_restricts_rhs_not_residual", "bc[lv->agg[i]] += b[i] - t[i];", "bc[lv->agg[i]] += b[i];"),
+    ("vcycle_post_sweep_forward", "for (int a = 0, z = n - 1; a < z; a++, z--)",
+     "for (int a = 0, z = n - 1; a < 0; a++, z--)"),
+    ("vcycle_coarse_mean_kept", "    for (int i = 0; i < n; i++) e[i] -= mu;\n", "    for (int i = 0; i < n; i++) e[i] -= 0.0 * mu;\n"),
+    ("vcycle_prolongation_wrong_level", "for (int i = 0; i < n; i++) e[i] += ec[lv->agg[i]];",
+     "for (int i = 0; i < n; i++) e[i] += ec[i % nc];"),
     ("lanczos_alpha_halved", "      al[j] = vdot(n, q, u);\n", "      al[j] = 0.5 * vdot(n, q, u);\n"),
     ("lanczos_largest_ritz_vector", "y += V[t * kk + 0] * Q[(size_t)t * n + i];",
      "y += V[t * kk + (kk - 1)] * Q[(size_t)t * n + i];"),

@@ -507,6 +507,8 @@ def test_paper_hec_order_is_sorted_splitmix_keys():
 
 
 REFINES = [oracle.REFINE_LOBPCG, oracle.REFINE_LANCZOS]
+# the LOBPCG preconditioners (reading R13); the Lanczos runs ignore it
+PRECONDS = [oracle.PRECOND_DEGREE, oracle.PRECOND_VCYCLE]
 RTIGHT = dict(refine_tol=1e-9, refine_max_iters=200000)
 
 
@@ -559,13 +561,14 @@ def test_refine_skewed_degrees():
     paper = oracle.solve(g)
     assert paper.lam > 1.5 * ev[1]
     its = {}
-    for refine in REFINES:
-        r = oracle.solve(g, refine=refine, refine_tol=1e-7, refine_max_iters=200000)
+    for refine, pre in ((oracle.REFINE_LOBPCG, oracle.PRECOND_DEGREE), (oracle.REFINE_LOBPCG, oracle.PRECOND_VCYCLE),
+                        (oracle.REFINE_LANCZOS, oracle.PRECOND_DEGREE)):
+        r = oracle.solve(g, refine=refine, refine_precond=pre, refine_tol=1e-7, refine_max_iters=200000)
         assert r.status == 0 and abs(r.lam - ev[1]) <= 1e-10 * ev[1], refine
-        its[refine] = r.refine_iters
+        its[(refine, pre)] = r.refine_iters
     # the D^-1 preconditioner evens out the spread of degrees: LOBPCG needs
     # far fewer matvecs than the unpreconditioned Krylov method
-    assert its[oracle.REFINE_LOBPCG] * 5 < its[oracle.REFINE_LANCZOS]
+    assert its[(oracle.REFINE_LOBPCG, oracle.PRECOND_DEGREE)] * 5 < its[(oracle.REFINE_LANCZOS, 0)]
 
 
 @pytest.mark.parametrize("refine", REFINES)
@@ -622,3 +625,78 @@ def test_refine_cap_and_degenerate_start():
         r = oracle.solve(inputs.complete(12), refine=refine)
         assert r.status == 0 and abs(r.lam - 12) <= 1e-12 * 12
         assert r.refine_iters <= 1
+
+
+# --------------------------------------------------------------------------
+# the V-cycle preconditioner (reading R13)
+
+def _dense_gs(A, d, b, e, order):
+    for i in order:
+        e[i] = (b[i] + A[i] @ e) / d[i]
+    return e
+
+
+def test_vcycle_two_levels_written_out():
+    """On a two-level hierarchy the V-cycle equals its definition written out
+    with dense matrices: forward colour sweep, aggregate sums of the residual,
+    20 forward sweeps and the mean removed on the coarse level, the correction
+    added to the members, backward colour sweep."""
+    g = inputs.random_connected(40, 3.0, seed=8)
+    run = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_forced=0)
+    assert run.num_levels == 2
+    f, c = run.level(0), run.level(1)
+    A0 = inputs.CSR(f.n, f.rowptr, f.col, f.w).dense()
+    A1 = inputs.CSR(c.n, c.rowptr, c.col, c.w).dense()
+    o0 = np.lexsort((np.arange(f.n), f.color))
+    o1 = np.lexsort((np.arange(c.n), c.color))
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(f.n)
+    b -= b.mean()
+    e = _dense_gs(A0, f.d, b, np.zeros(f.n), o0)
+    res = b - (np.diag(f.d) - A0) @ e
+    bc = np.zeros(c.n)
+    np.add.at(bc, f.agg, res)
+    ec = np.zeros(c.n)
+    for _ in range(20):
+        _dense_gs(A1, c.d, bc, ec, o1)
+    ec -= ec.mean()
+    e = e + ec[f.agg]
+    e = _dense_gs(A0, f.d, b, e, o0[::-1])
+    got = run.vcycle(b)
+    assert np.allclose(got, e, rtol=1e-12, atol=1e-14)
+
+
+def test_vcycle_is_a_contracting_approximate_inverse():
+    """On a weighted grid one V-cycle removes most of the error of L e = b for
+    b orthogonal to 1 (measured against the dense pseudo-inverse solution)."""
+    g = inputs.grid(30, 22, "uniform", seed=5)
+    run = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_forced=0)
+    assert run.num_levels >= 3
+    L = laplacian_dense(g)
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        b = rng.standard_normal(g.n)
+        b -= b.mean()
+        exact = np.linalg.pinv(L) @ b
+        e = run.vcycle(b)
+        e -= e.mean()
+        assert np.linalg.norm(L @ (e - exact)) < 0.6 * np.linalg.norm(b)
+
+
+def test_vcycle_preconditioning_cuts_lobpcg_steps_on_grids():
+    g = inputs.grid(90, 61, "uniform", seed=4)
+    its = {}
+    for pre in PRECONDS:
+        r = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_precond=pre, refine_tol=1e-6,
+                         refine_max_iters=100000)
+        assert r.status == 0 and not r.capped
+        its[pre] = r.refine_iters
+    assert its[oracle.PRECOND_VCYCLE] * 5 < its[oracle.PRECOND_DEGREE]
+
+
+@pytest.mark.parametrize("pre", PRECONDS)
+def test_lobpcg_both_preconditioners_reach_dense_jacobi(pre):
+    g = inputs.random_connected(190, 5.0, seed=11)
+    ev, V, _ = oracle.jacobi_eig(laplacian_dense(g))
+    r = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_precond=pre, refine_tol=1e-8, refine_max_iters=100000)
+    assert r.status == 0 and abs(r.lam - ev[1]) <= 1e-12 * ev[1]
