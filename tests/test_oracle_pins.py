@@ -601,18 +601,20 @@ def test_refine_forced_count_replays(refine):
         assert (np.linalg.norm(Ld @ x - th * x) <= 1.001 * tol * th) == ok
 
 
-def test_lobpcg_stops_at_the_rounding_floor():
-    """With a tolerance below reach, LOBPCG stops at the first step whose
-    Rayleigh quotient is not below the previous one: lambda_2 is exact to
-    rounding there, and one step earlier the quotient was still falling."""
+@pytest.mark.parametrize("pre", [0, 1])
+def test_lobpcg_stops_at_the_rounding_floor(pre):
+    """With a tolerance below reach, LOBPCG ends at the rounding floor (a step
+    without p that does not lower the Rayleigh quotient), long before its cap,
+    with lambda_2 exact to rounding; replaying its count gives the same bits
+    (the restarts without p are part of the step sequence)."""
     g = inputs.grid(33, 19, "uniform", seed=12)
-    free = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_tol=1e-14, refine_max_iters=100000)
-    assert not free.capped
-    k = free.refine_iters
+    free = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_precond=pre, refine_tol=1e-15,
+                        refine_max_iters=100000)
+    assert not free.capped and free.refine_iters < 2000
     ev = np.linalg.eigvalsh(laplacian_dense(g))
     assert abs(free.lam - ev[1]) <= 1e-13 * ev[1]
-    lams = [oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_forced=j).lam for j in (k - 2, k - 1, k)]
-    assert lams[1] < lams[0]
+    again = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_precond=pre, refine_forced=free.refine_iters)
+    assert again.lam == free.lam
 
 
 def test_refine_cap_and_degenerate_start():
@@ -700,3 +702,30 @@ def test_lobpcg_both_preconditioners_reach_dense_jacobi(pre):
     ev, V, _ = oracle.jacobi_eig(laplacian_dense(g))
     r = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_precond=pre, refine_tol=1e-8, refine_max_iters=100000)
     assert r.status == 0 and abs(r.lam - ev[1]) <= 1e-12 * ev[1]
+
+
+@pytest.mark.parametrize("pre", [0, 1])
+def test_lobpcg_first_step_written_out(pre):
+    """One LOBPCG step from the cascade's start, written out: w = M r with its
+    mean removed (M = D^-1 or one V-cycle), r = L x - theta x, then the
+    smallest Rayleigh-Ritz pair of span{x, w} (dense generalized eigenproblem),
+    the Ritz vector deflated, normalised and sign-normalised."""
+    import scipy.linalg as sla
+    g = inputs.grid(24, 17, "uniform", seed=6)
+    Ld = laplacian_dense(g)
+    d = np.diag(Ld)
+    r0 = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_precond=pre, refine_forced=0)
+    x = r0.x(g.n)
+    th = x @ Ld @ x / (x @ x)
+    r = Ld @ x - th * x
+    w = r / d if pre == 0 else r0.vcycle(r)
+    w -= w.mean()
+    S = np.stack([x, w], axis=1)
+    ev, V = sla.eigh(S.T @ Ld @ S, S.T @ S)
+    x1 = S @ V[:, 0]
+    x1 -= x1.mean()
+    x1 /= np.linalg.norm(x1)
+    if x1[np.argmax(np.abs(x1))] < 0:
+        x1 = -x1
+    r1 = oracle.solve(g, refine=oracle.REFINE_LOBPCG, refine_precond=pre, refine_forced=1)
+    assert np.allclose(r1.x(g.n), x1, rtol=0, atol=1e-10)
