@@ -75,11 +75,11 @@
  *       until ||L x - theta x|| <= refine_tol * theta * ||x|| (LOBPCG: tested
  *       before every step; Lanczos: the Ritz estimate beta_m |s_m| at the end
  *       of a cycle), or refine_max_iters matvecs.  In exact arithmetic each
- *       Rayleigh-Ritz step lowers the Rayleigh quotient; a step that does not
- *       (rounding) restarts LOBPCG without p when it used p, and ends the
- *       iteration when it did not: the rounding floor of the arithmetic (in
- *       float the residual stalls near 1e-3 theta on graphs of small lambda_2
- *       while lambda_2 itself is already exact to ~1e-8).
+ *       Rayleigh-Ritz step lowers the Rayleigh quotient; a step that brings no
+ *       new lowest value (rounding) restarts LOBPCG without p, and three such
+ *       steps in a row end the iteration: the rounding floor of the arithmetic
+ *       (in float the residual stalls near 1e-3 theta on graphs of small
+ *       lambda_2 while lambda_2 itself is already exact to ~1e-8).
  *   R13 LOBPCG's preconditioner (refine_precond; not in the paper): D^-1, or
  *       one V-cycle of the cascade's own hierarchy on L e = r: on level l, one
  *       forward Gauss-Seidel sweep from e = 0 (colour classes ascending), the
@@ -976,9 +976,9 @@ static int refine_lobpcg(const oracle_run *run, orc_level *lv, double *x, const 
     free(lx); free(w); free(lw); free(p); free(lp); free(xn);
     return ORC_ENOMEM;
   }
-  int forced = o->refine_forced, pvalid = 0, p_used = 0, k = 0;
+  int forced = o->refine_forced, pvalid = 0, flat = 0, k = 0;
   lap_apply(L, x, lx);
-  double theta = vdot(n, x, lx) / vdot(n, x, x), theta_prev = 0.0;
+  double theta = vdot(n, x, lx) / vdot(n, x, x), theta_best = 0.0;
   for (;;) {
     double rr = 0.0;
     for (int i = 0; i < n; i++) {
@@ -986,15 +986,17 @@ static int refine_lobpcg(const oracle_run *run, orc_level *lv, double *x, const 
       rr += w[i] * w[i];
     }
     if (forced < 0 && sqrt(rr) <= o->refine_tol * theta * sqrt(vdot(n, x, x))) break;
-    /* no descent (only rounding can cause it): a step that used p restarts
-     * without it; a step on [x, w] alone ends the iteration */
-    if (k > 0 && theta >= theta_prev) {
-      if (forced < 0 && !p_used) break;
+    /* no new lowest Rayleigh quotient (only rounding can cause it): restart
+     * without p; three such steps in a row end the iteration */
+    if (k == 0 || theta < theta_best) {
+      theta_best = theta;
+      flat = 0;
+    } else {
       pvalid = 0;
+      if (++flat >= 3 && forced < 0) break;
     }
     if (forced >= 0 && k >= forced) break;
     if (forced < 0 && k >= o->refine_max_iters) { lv->capped = 1; break; }
-    theta_prev = theta;
     if (o->refine_precond == 1) {
       memcpy(xn, w, sizeof(double) * (size_t)n);
       int vst = vcycle(run, 0, xn, w);
@@ -1006,7 +1008,6 @@ static int refine_lobpcg(const oracle_run *run, orc_level *lv, double *x, const 
     for (int i = 0; i < n; i++) w[i] -= mw;
     lap_apply(L, w, lw);
     k++;
-    p_used = pvalid;
     double *Sv[3] = {x, w, p}, *LS[3] = {lx, lw, lp};
     double c[3];
     int kept = rayleigh_ritz(n, Sv, LS, pvalid ? 3 : 2, c);

@@ -71,8 +71,8 @@ MUTANTS = [
      "for (int i = 0; i < m; i++) y += Rinv[i][a] * V[i * m + (m - 1)];"),
     ("lobpcg_stop_rule_absolute", "sqrt(rr) <= o->refine_tol * theta * sqrt(vdot(n, x, x))",
      "sqrt(rr) <= o->refine_tol * sqrt(vdot(n, x, x))"),
-    ("lobpcg_stall_rule_loose", "if (k > 0 && theta >= theta_prev) {",
-     "if (k > 0 && theta >= theta_prev * (1.0 - 1e-3)) {"),
+    ("lobpcg_stall_rule_loose", "if (k == 0 || theta < theta_best) {",
+     "if (k == 0 || theta < theta_best * (1.0 - 1e-3)) {"),
     ("vcycle_restricts_rhs_not_residual", "bc[lv->agg[i]] += b[i] - t[i];", "bc[lv->agg[i]] += b[i];"),
     ("vcycle_post_sweep_forward", "for (int a = 0, z = n - 1; a < z; a++, z--)",
      "for (int a = 0, z = n - 1; a < 0; a++, z--)"),
