@@ -76,7 +76,7 @@
  *       before every step; Lanczos: the Ritz estimate beta_m |s_m| at the end
  *       of a cycle), or refine_max_iters matvecs.  In exact arithmetic each
  *       Rayleigh-Ritz step lowers the Rayleigh quotient; a step that brings no
- *       new lowest value (rounding) restarts LOBPCG without p, and three such
+ *       new lowest value (rounding) restarts LOBPCG without p, and eight such
  *       steps in a row end the iteration: the rounding floor of the arithmetic
  *       (in float the residual stalls near 1e-3 theta on graphs of small
  *       lambda_2 while lambda_2 itself is already exact to ~1e-8).
@@ -987,13 +987,13 @@ static int refine_lobpcg(const oracle_run *run, orc_level *lv, double *x, const 
     }
     if (forced < 0 && sqrt(rr) <= o->refine_tol * theta * sqrt(vdot(n, x, x))) break;
     /* no new lowest Rayleigh quotient (only rounding can cause it): restart
-     * without p; three such steps in a row end the iteration */
+     * without p; eight such steps in a row end the iteration */
     if (k == 0 || theta < theta_best) {
       theta_best = theta;
       flat = 0;
     } else {
       pvalid = 0;
-      if (++flat >= 3 && forced < 0) break;
+      if (++flat >= 8 && forced < 0) break;
     }
     if (forced >= 0 && k >= forced) break;
     if (forced < 0 && k >= o->refine_max_iters) { lv->capped = 1; break; }
