@@ -67,7 +67,7 @@ enum { FIEDLER_W_F32 = 0, FIEDLER_W_F64 = 1 };
  * smoother as future work; the cosine test stops power iteration long before
  * the residual is small on graphs with a wide spread of degrees):
  *  - LOBPCG: single-vector locally optimal preconditioned conjugate gradient
- *    (Knyazev, 2001) on 1-perp, preconditioned by the inverse degree D^-1;
+ *    (Knyazev, 2001) on 1-perp, preconditioned as refine_precond says;
  *  - LANCZOS: Lanczos with full reorthogonalisation on 1-perp, restarted from
  *    the Ritz vector every lanczos_basis steps. */
 enum { FIEDLER_REFINE_NONE = 0, FIEDLER_REFINE_LOBPCG = 1, FIEDLER_REFINE_LANCZOS = 2 };
@@ -78,6 +78,14 @@ enum { FIEDLER_REFINE_NONE = 0, FIEDLER_REFINE_LOBPCG = 1, FIEDLER_REFINE_LANCZO
  * joining that neighbour's aggregate; the order on level l is the ascending
  * order of the keys splitmix64(seed + l, v) (ties by v). */
 enum { FIEDLER_HEC_DOMINANT = 0, FIEDLER_HEC_PAPER = 1 };
+/* fiedler_options.refine_precond: LOBPCG's preconditioner.  DEGREE: D^-1.
+ * VCYCLE (default): one V-cycle of the cascade's own hierarchy on L e = r
+ * (a project addition; the paper has no preconditioner): one forward
+ * Gauss-Seidel sweep from e = 0 per level (colour classes ascending), the
+ * residual summed over each aggregate as the next level's right-hand side,
+ * 20 sweeps and the mean removed on the coarsest level, the correction added
+ * to every member, one backward sweep (classes descending). */
+enum { FIEDLER_PRECOND_DEGREE = 0, FIEDLER_PRECOND_VCYCLE = 1 };
 
 typedef struct {
   int precision;             /* FIEDLER_FP64: values and arithmetic in double.
@@ -118,6 +126,13 @@ typedef struct {
                                 theta = x^T L x / x^T x */
   int lanczos_basis;         /* FIEDLER_REFINE_LANCZOS: basis vectors per restart cycle, 4..64 */
   int hec_mode;              /* FIEDLER_HEC_DOMINANT (default) or FIEDLER_HEC_PAPER */
+  int refine_precond;        /* FIEDLER_PRECOND_VCYCLE (default) or FIEDLER_PRECOND_DEGREE */
+  int lane_sms;              /* serving form (a project addition): SMs whose block slots the
+                                serving kernel leaves to a lane for large graphs, which solves
+                                them one at a time with the cooperative grid-wide kernels on
+                                that many SMs (2 blocks per SM); 0 = no lane (default), at most
+                                half the device's SMs */
+  int lane_min_n;            /* graphs with at least this many vertices take the lane (if any) */
 } fiedler_options;
 
 typedef struct {
@@ -157,7 +172,8 @@ typedef struct fiedler_plan fiedler_plan;
  * validate 1, tail_max_n 4096, tail_max_nnz 32768, barrier_timeout_ms 5000, fault_inject 0,
  * hbm_budget_bytes 0 (16 GiB), max_batch 1024, queue_budget_bytes 0 (8 GiB),
  * batch_threads 0, refine NONE, refine_max_iters 5000, refine_tol 1e-4,
- * lanczos_basis 24, hec_mode DOMINANT. */
+ * lanczos_basis 24, hec_mode DOMINANT, refine_precond VCYCLE, lane_sms 0,
+ * lane_min_n 200000. */
 void fiedler_options_default(fiedler_options *opts);
 
 /* Creates a plan on the current CUDA device.  opts may be NULL (defaults);
@@ -229,6 +245,34 @@ void fiedler_plan_destroy(fiedler_plan *plan);
 
 /* Static English description of a status. */
 const char *fiedler_status_str(fiedler_status status);
+
+/* ---- spectral partitioning ---------------------------------------------- */
+
+typedef struct {
+  int parts;                 /* parts produced (fewer than asked only when every part left is a
+                                single vertex) */
+  int solves;                /* Fiedler solves run (one per split) */
+  int component_splits;      /* splits made along connected components (disconnected parts) */
+  float ms;                  /* wall time of the call */
+} fiedler_partition_info;
+
+/* Spectral partitioning by recursive Fiedler bisection, the application the
+ * paper's Introduction names (partitioning a graph by its Fiedler vector; a
+ * project addition in this form).  Every vertex starts in part 0; until
+ * `parts` parts exist, the part with the most vertices (lowest part id on
+ * ties) is split: its induced subgraph is extracted on the device and solved
+ * with the plan's options, and its vertices with x_i < 0 (x sign-normalised as
+ * fiedler_result.x) form the new part, numbered in order of creation.  A part
+ * whose subgraph is disconnected is split along its components instead: the
+ * component of its lowest vertex stays, the rest forms the new part.
+ *  - graph: host or device CSR as for fiedler_solve.
+ *  - labels: n int32 (host, or device if labels_on_device), the part of every
+ *    vertex on return.  info may be NULL.
+ * Errors: those of fiedler_solve for the first split that fails; EINVAL for
+ * parts < 1.  The plan's last-solve introspection then describes the last
+ * split's subgraph. */
+fiedler_status fiedler_partition(fiedler_plan *plan, const fiedler_graph *graph, int parts, int32_t *labels,
+                                 int labels_on_device, fiedler_partition_info *info);
 
 /* ---- introspection of the last solve (tests, profiling) ---------------- */
 

@@ -28,6 +28,7 @@
 #include "fz_state.h"
 #include "host_opts.h"
 #include "kernels.h"
+#include "partition.h"
 
 using fz::State;
 
@@ -52,6 +53,7 @@ struct Ticket {
   fiedler_result res{};
   fiedler_status st = FIEDLER_EAGAIN;
   bool done = false, canceled = false, running = false;
+  bool lane = false;      // solved by the large-graph lane, not the serving ring
 };
 
 // One graph of a batched launch.
@@ -84,6 +86,7 @@ struct BatchCtx {
   size_t footprint = 0;
   bool busy = false;
   int type = 1;
+  int reserve_sms = 0;  // SMs whose block slots the launch leaves free (the large-graph lane)
   // layout (offsets in d_buf / h_buf)
   size_t d_states, d_counter, d_scratch, slot_bytes, d_arena, d_in, d_x, d_total;
   size_t h_states, h_in, h_x, h_total, in_bytes, x_bytes;
@@ -145,6 +148,19 @@ struct fiedler_plan {
   State *h_stage = nullptr;           // pinned staging of ticket states (max_batch of them)
   int stage_n = 0;
   std::deque<Ticket *> live;          // published, not yet finished (ring order)
+  // large-graph lane of the serving form: admitted large tickets wait in
+  // lane_q and run one at a time through the cooperative grid-wide kernels on
+  // lane_blocks blocks (lane_sms SMs) on the lane's own stream
+  struct Lane {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    fz::IRed *ipart = nullptr;
+    double *dpart = nullptr;
+    int blocks[2] = {0, 0};  // [type] blocks of one lane launch
+    Ticket *cur = nullptr;
+    std::deque<Ticket *> q;
+    uint64_t solves = 0;
+  } lane;
   uint64_t n_launches = 0;
   // serving form
   std::mutex exec_mu;       // one solve on the device state at a time
@@ -207,7 +223,7 @@ size_t arena_estimate(int64_t n, int64_t nnz, size_t tsz, bool wf64, const fiedl
                      (2.0 * tsz + 4.0) * n) +
               fz::kMaxLevels * 4.0 * (fz::kMaxColors + 1);
   double slack = fz::kMaxLevels * 24.0 * 256.0 + (1 << 20);
-  return (size_t)(l0 + lc + slack) + fz::refine_bytes(n, tsz, o.refine, o.lanczos_basis);
+  return (size_t)(l0 + lc + slack) + fz::refine_bytes(n, tsz, o.refine, o.lanczos_basis, o.refine_precond);
 }
 
 size_t scratch_estimate(int64_t n, int64_t nnz, int nblocks, const fiedler_options &o) {
@@ -251,7 +267,9 @@ bool options_valid(const fiedler_options &o) {
            (o.refine != FIEDLER_REFINE_NONE && o.refine != FIEDLER_REFINE_LOBPCG &&
             o.refine != FIEDLER_REFINE_LANCZOS) ||
            o.refine_max_iters < 0 || !(o.refine_tol > 0.0 && o.refine_tol < 1.0) || o.lanczos_basis < 4 ||
-           o.lanczos_basis > fz::kMaxBasis || (o.hec_mode != FIEDLER_HEC_DOMINANT && o.hec_mode != FIEDLER_HEC_PAPER));
+           o.lanczos_basis > fz::kMaxBasis || (o.hec_mode != FIEDLER_HEC_DOMINANT && o.hec_mode != FIEDLER_HEC_PAPER) ||
+           (o.refine_precond != FIEDLER_PRECOND_DEGREE && o.refine_precond != FIEDLER_PRECOND_VCYCLE) ||
+           o.lane_sms < 0 || o.lane_min_n < 2);
 }
 
 void fill_opts(fz::Opts &o, const fiedler_options &u, int type) {
@@ -278,6 +296,7 @@ void fill_opts(fz::Opts &o, const fiedler_options &u, int type) {
   o.refine_max_iters = u.refine_max_iters;
   o.lanczos_basis = u.lanczos_basis;
   o.hec_mode = u.hec_mode;
+  o.refine_precond = u.refine_precond;
   o.refine_tol = u.refine_tol;
 }
 
@@ -504,7 +523,8 @@ fiedler_status batch_launch(fiedler_plan *p, BatchCtx &c, double arena_scale) {
                    [](const BatchItem &a, const BatchItem &b) { return a.nnz + a.n > b.nnz + b.n; });
   const int count = (int)c.items.size();
   const int var = p->batch_var;
-  const int nslots = std::min(count, p->batch_slots[type][var]);
+  const int per_sm = std::max(1, p->batch_slots[type][var] / p->sms);
+  const int nslots = std::min(count, std::max(per_sm, p->batch_slots[type][var] - per_sm * c.reserve_sms));
   size_t slot = 0, arenas = 0, in_b = 0, x_b = 0;
   for (auto &it : c.items) {
     it.arena_b = r256((size_t)(arena_estimate(it.n, it.nnz, tsz, it.wf64, p->opt) * arena_scale));
@@ -828,6 +848,64 @@ void worker_main(fiedler_plan *p) {
         p->q_cv.notify_all();
       }
     }
+    // 1b. the large-graph lane: its finished ticket, then the next one
+    if (p->lane.cur && cudaEventQuery(p->lane.ev) == cudaSuccess) {
+      progressed = true;
+      Ticket *t = p->lane.cur;
+      p->lane.cur = nullptr;
+      const bool ok = cudaMemcpyAsync(p->h_stage, t->dwork, sizeof(State), cudaMemcpyDeviceToHost,
+                                      p->lane.stream) == cudaSuccess &&
+                      cudaStreamSynchronize(p->lane.stream) == cudaSuccess;
+      const State *h = p->h_stage;
+      const auto now = std::chrono::steady_clock::now();
+      std::lock_guard<std::mutex> lk(p->q_mu);
+      cudaFreeAsync(t->dwork, p->lane.stream);
+      t->dwork = nullptr;
+      p->inflight_bytes -= t->footprint;
+      if (ok && (h->status == fz::ST_ARENA || h->status == fz::ST_SCRATCH) && t->scale < 8.0) {
+        t->scale *= 2.0;  // the hierarchy outgrew its estimate: run it again with more room
+        t->running = false;
+        p->queue.push_front(t->id);
+      } else {
+        if (ok) ticket_result(h, t);
+        else t->st = FIEDLER_ECUDA;
+        if (ok && (h->status == fz::ST_ARENA || h->status == fz::ST_SCRATCH)) t->st = FIEDLER_ENOMEM;
+        mark_done(p, t);
+        t->running = false;
+        p->n_completed++;
+        p->lane.solves++;
+        p->latencies_ms.push_back(std::chrono::duration<float, std::milli>(now - t->t_submit).count());
+      }
+      p->q_cv.notify_all();
+    }
+    if (!p->lane.cur && !p->lane.q.empty()) {
+      progressed = true;
+      Ticket *t = p->lane.q.front();
+      p->lane.q.pop_front();
+      const fz::KernelSet &K = p->ks[type];
+      const int nbl = p->lane.blocks[type];
+      void *args[] = {(void *)&t->dwork};
+      const bool ok =
+          cudaLaunchCooperativeKernel(K.grid_setup, dim3(nbl), dim3(fz::kGridThreads), args, 0, p->lane.stream) ==
+              cudaSuccess &&
+          cudaLaunchKernel(K.cta, dim3(1), dim3(fz::kCtaThreads), args, 0, p->lane.stream) == cudaSuccess &&
+          cudaLaunchCooperativeKernel(K.grid_solve, dim3(nbl), dim3(fz::kGridThreads), args, 0, p->lane.stream) ==
+              cudaSuccess &&
+          cudaEventRecord(p->lane.ev, p->lane.stream) == cudaSuccess;
+      if (ok) {
+        p->lane.cur = t;
+        p->n_launches += 3;
+      } else {
+        std::lock_guard<std::mutex> lk(p->q_mu);
+        cudaFreeAsync(t->dwork, p->lane.stream);
+        t->dwork = nullptr;
+        p->inflight_bytes -= t->footprint;
+        t->st = FIEDLER_ECUDA;
+        mark_done(p, t);
+        t->running = false;
+        p->q_cv.notify_all();
+      }
+    }
     // 2. admissions
     adm.clear();
     {
@@ -848,9 +926,11 @@ void worker_main(fiedler_plan *p) {
           continue;
         }
         // footprint with the learned arena factor (a rerun doubles t->scale)
+        t->lane = p->lane.stream && t->n >= p->opt.lane_min_n;
         t->learn = p->arena_factor();
         t->arena_b = r256((size_t)(arena_estimate(t->n, t->nnz, tsz, t->w_dtype == FIEDLER_W_F64, p->opt) * t->scale * t->learn));
-        t->scratch_b = r256((size_t)(scratch_estimate(t->n, t->nnz, 1, p->opt) * t->scale));
+        t->scratch_b = r256((size_t)(scratch_estimate(t->n, t->nnz, t->lane ? p->lane.blocks[type] : 1, p->opt) *
+                                     t->scale));
         t->footprint = r256(sizeof(State)) + t->arena_b + t->scratch_b;
         const bool empty = p->inflight_bytes == 0 && adm.empty();
         if (!empty && p->inflight_bytes + t->footprint > budget) break;  // wait for memory to free up
@@ -880,8 +960,15 @@ void worker_main(fiedler_plan *p) {
         }
         State *h = p->h_stage + staged++;
         fill_ticket_state(p, t, h, type, ab, sb);
+        if (t->lane) {  // the grid-wide engine on the large levels, with the lane's partials
+          h->opt.tail_max_n = p->opt.tail_max_n;
+          h->opt.tail_max_nnz = p->opt.tail_max_nnz;
+          h->ipart = p->lane.ipart;
+          h->dpart = p->lane.dpart;
+        }
         cudaMemcpyAsync(t->dwork, h, sizeof(State), cudaMemcpyHostToDevice, p->io_stream);
-        ok_t.push_back(t);
+        if (t->lane) p->lane.q.push_back(t);
+        else ok_t.push_back(t);
       }
       // item pointers, then the new tail, in stream order after the states
       const unsigned long long first = p->published;
@@ -936,7 +1023,9 @@ void worker_main(fiedler_plan *p) {
       for (Ticket *t : p->live) unfinished += vd->done[t->k % fz::kRing] != t->k + 1ull;
       const int var = p->batch_var;
       const int slots = p->serve_slots[type][var], per_sm = slots / p->sms;
-      const int room = std::max(per_sm, slots - per_sm * fiedler_plan::kReserveSms) - alive;
+      const int room =
+          std::max(per_sm, slots - per_sm * (fiedler_plan::kReserveSms + (p->lane.stream ? p->opt.lane_sms : 0))) -
+          alive;
       p->live_sum += (double)unfinished;
       p->alive_sum += (double)alive;
       p->live_rounds++;
@@ -974,7 +1063,8 @@ void worker_main(fiedler_plan *p) {
     if (!progressed) {
       std::unique_lock<std::mutex> lk(p->q_mu);
       if (p->stop) break;
-      if (p->live.empty() && p->queue.empty()) p->q_cv.wait(lk, [&] { return p->stop || !p->queue.empty(); });
+      if (p->live.empty() && p->queue.empty() && !p->lane.cur && p->lane.q.empty())
+        p->q_cv.wait(lk, [&] { return p->stop || !p->queue.empty(); });
       else p->q_cv.wait_for(lk, std::chrono::microseconds(50));
     }
   }
@@ -988,11 +1078,138 @@ void worker_main(fiedler_plan *p) {
     if (L.running) cudaEventSynchronize(L.ev);
     L.running = false;
   }
+  if (p->lane.cur) {
+    cudaEventSynchronize(p->lane.ev);
+    p->live.push_back(p->lane.cur);  // released below
+    p->lane.cur = nullptr;
+  }
+  for (Ticket *t : p->lane.q) p->live.push_back(t);
+  p->lane.q.clear();
   for (Ticket *t : p->live) {
     if (t->dwork) cudaFreeAsync(t->dwork, p->io_stream);
     t->dwork = nullptr;
   }
   p->live.clear();
+}
+
+}  // namespace
+
+namespace {
+
+// Recursive spectral bisection on the plan (the plan's exec lock held): the
+// largest part with at least two vertices (lowest id on ties) is split by the
+// sign of the Fiedler vector of its induced subgraph, or along its connected
+// components when that subgraph is disconnected, until `parts` parts exist.
+fiedler_status partition_locked(fiedler_plan *p, const fiedler_graph *g, int parts, int32_t *labels, int lab_dev,
+                                fiedler_partition_info *info) {
+  const int64_t n = g->n, nnz = g->nnz;
+  const size_t wsz = g->w_dtype == FIEDLER_W_F64 ? 8 : 4;
+  cudaStream_t st = p->stream;
+  // device copies of the input (if on the host), the labels, the subgraph
+  // buffers and the scratch: one allocation
+  const size_t in_b = g->on_device ? 0 : r256(4 * (size_t)(n + 1)) + r256(4 * (size_t)std::max<int64_t>(nnz, 1)) +
+                                          r256(wsz * (size_t)std::max<int64_t>(nnz, 1));
+  const size_t sub_b = r256(4 * (size_t)(n + 1)) + r256(4 * (size_t)std::max<int64_t>(nnz, 1)) +
+                       r256(wsz * (size_t)std::max<int64_t>(nnz, 1)) + r256(4 * (size_t)n) + r256(8 * (size_t)n) +
+                       r256(4 * (size_t)n) + r256(4 * fz::part_scratch_ints(n)) + r256(4 * (size_t)n);
+  char *buf = nullptr;
+  CK(cudaMallocAsync((void **)&buf, in_b + sub_b, st));
+  int *h = nullptr;
+  cudaError_t he = cudaMallocHost((void **)&h, 4 * sizeof(int));
+  if (he != cudaSuccess) {
+    cudaFreeAsync(buf, st);
+    return map_cuda(he);
+  }
+  auto cleanup = [&](fiedler_status rs) {
+    cudaFreeAsync(buf, st);
+    cudaStreamSynchronize(st);
+    cudaFreeHost(h);
+    return rs;
+  };
+  char *q = buf;
+  auto take = [&](size_t b) {
+    char *r = q;
+    q += r256(b);
+    return r;
+  };
+  const int32_t *rp = g->rowptr, *ci = g->col;
+  const void *w = g->w;
+  if (!g->on_device) {
+    int32_t *drp = (int32_t *)take(4 * (size_t)(n + 1));
+    int32_t *dci = (int32_t *)take(4 * (size_t)std::max<int64_t>(nnz, 1));
+    void *dw = take(wsz * (size_t)std::max<int64_t>(nnz, 1));
+    if (cudaMemcpyAsync(drp, rp, 4 * (size_t)(n + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        (nnz > 0 && (cudaMemcpyAsync(dci, ci, 4 * (size_t)nnz, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                     cudaMemcpyAsync(dw, w, wsz * (size_t)nnz, cudaMemcpyHostToDevice, st) != cudaSuccess)))
+      return cleanup(FIEDLER_ECUDA);
+    rp = drp;
+    ci = dci;
+    w = dw;
+  }
+  int32_t *srp = (int32_t *)take(4 * (size_t)(n + 1));
+  int32_t *sci = (int32_t *)take(4 * (size_t)std::max<int64_t>(nnz, 1));
+  void *sw = take(wsz * (size_t)std::max<int64_t>(nnz, 1));
+  int32_t *map = (int32_t *)take(4 * (size_t)n);
+  double *x = (double *)take(8 * (size_t)n);
+  int32_t *comp = (int32_t *)take(4 * (size_t)n);
+  int *sc = (int *)take(4 * fz::part_scratch_ints(n));
+  int32_t *lab = (int32_t *)take(4 * (size_t)n);
+  fz::PartScratch ps;
+  ps.keep = sc;
+  ps.cnt = sc + (n + 1);
+  ps.bsum = sc + 2 * (n + 1);
+  ps.flag = sc + fz::part_scratch_ints(n) - 2;
+  if (cudaMemsetAsync(lab, 0, 4 * (size_t)n, st) != cudaSuccess) return cleanup(FIEDLER_ECUDA);
+  std::vector<int64_t> size(1, n);
+  std::vector<char> stuck(1, 0);
+  int solves = 0, comp_splits = 0;
+  const auto t0 = std::chrono::steady_clock::now();
+  fiedler_status out = FIEDLER_OK;
+  while ((int)size.size() < parts) {
+    int pick = -1;
+    for (int k = 0; k < (int)size.size(); k++)
+      if (!stuck[k] && size[k] >= 2 && (pick < 0 || size[k] > size[pick])) pick = k;
+    if (pick < 0) break;  // every part is a single vertex or cannot be split
+    const int newp = (int)size.size();
+    if (fz::part_extract(rp, ci, w, wsz == 8, n, lab, pick, srp, sci, sw, map, ps, h, st) != cudaSuccess)
+      return cleanup(FIEDLER_ECUDA);
+    const int64_t m = h[0], mnz = h[1];
+    fiedler_result res{};
+    fiedler_status sst = run_solve(p, m, mnz, srp, sci, sw, wsz == 8, x, &res);
+    solves++;
+    cudaError_t ce;
+    if (sst == FIEDLER_OK || sst == FIEDLER_ENOTCONVERGED) {
+      ce = fz::part_split_sign(x, m, map, lab, newp, ps, &h[2], st);
+    } else if (sst == FIEDLER_EDISCONNECTED) {
+      ce = fz::part_split_components(srp, sci, m, map, lab, newp, comp, ps, &h[2], st);
+      comp_splits++;
+    } else {
+      out = sst;
+      break;
+    }
+    if (ce != cudaSuccess) return cleanup(FIEDLER_ECUDA);
+    const int64_t moved = h[2];
+    if (moved <= 0 || moved >= size[pick]) {  // nothing to split off (cannot happen for x orthogonal to 1)
+      stuck[pick] = 1;
+      continue;
+    }
+    size[pick] -= moved;
+    size.push_back(moved);
+    stuck.push_back(0);
+  }
+  if (out == FIEDLER_OK) {
+    if (cudaMemcpyAsync(labels, lab, 4 * (size_t)n, lab_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess)
+      return cleanup(FIEDLER_ECUDA);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cleanup(FIEDLER_ECUDA);
+  if (info) {
+    info->parts = (int)size.size();
+    info->solves = solves;
+    info->component_splits = comp_splits;
+    info->ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return cleanup(out);
 }
 
 }  // namespace
@@ -1027,6 +1244,9 @@ void fiedler_options_default(fiedler_options *o) {
   o->refine_tol = 1e-4;
   o->lanczos_basis = 24;
   o->hec_mode = FIEDLER_HEC_DOMINANT;
+  o->refine_precond = FIEDLER_PRECOND_VCYCLE;
+  o->lane_sms = 0;
+  o->lane_min_n = 200000;
 }
 
 fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_stream, fiedler_plan **out) {
@@ -1079,6 +1299,18 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
       p->serve_slots[t][v] = bps * p->sms;
     }
   p->batch_var = o.batch_threads == 256 ? 1 : o.batch_threads == 128 ? 2 : 0;
+  if (o.lane_sms > 0) {
+    if (o.lane_sms > p->sms / 2) return fail(FIEDLER_EINVAL);
+    for (int t = 0; t < 2; t++) {
+      const int bps = std::min(p->grid_blocks[t][0], p->grid_blocks[t][1]) / p->sms;
+      p->lane.blocks[t] = std::max(1, bps) * o.lane_sms;
+    }
+    if (cudaStreamCreateWithFlags(&p->lane.stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FIEDLER_ECUDA);
+    if (cudaEventCreateWithFlags(&p->lane.ev, cudaEventDisableTiming) != cudaSuccess) return fail(FIEDLER_ECUDA);
+    if (cudaMalloc(&p->lane.ipart, sizeof(fz::IRed) * 2 * fz::kMaxBlocks) != cudaSuccess) return fail(FIEDLER_ENOMEM);
+    if (cudaMalloc(&p->lane.dpart, sizeof(double) * 2 * fz::kMaxBlocks * fz::kDSum) != cudaSuccess)
+      return fail(FIEDLER_ENOMEM);
+  }
   p->bsync.stream = p->stream;
   if (cudaEventCreateWithFlags(&p->bsync.done, cudaEventDisableTiming) != cudaSuccess) return fail(FIEDLER_ECUDA);
   if (cudaHostAlloc((void **)&p->done, sizeof(fz::ServeDone), cudaHostAllocMapped) != cudaSuccess)
@@ -1117,6 +1349,15 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
   p->worker = std::thread(worker_main, p);
   *out = p;
   return FIEDLER_OK;
+}
+
+fiedler_status fiedler_partition(fiedler_plan *p, const fiedler_graph *g, int parts, int32_t *labels,
+                                 int labels_on_device, fiedler_partition_info *info) {
+  if (!p || !labels || parts < 1) return FIEDLER_EINVAL;
+  fiedler_status st = check_graph(g, nullptr);
+  if (st != FIEDLER_OK) return st;
+  std::lock_guard<std::mutex> ex(p->exec_mu);
+  return partition_locked(p, g, parts, labels, labels_on_device, info);
 }
 
 fiedler_status fiedler_solve(fiedler_plan *p, const fiedler_graph *g, fiedler_result *res) {
@@ -1187,6 +1428,143 @@ fiedler_status fiedler_batch_submit(fiedler_plan *p, const fiedler_graph *g, uin
   return FIEDLER_OK;
 }
 
+namespace {
+
+// The large graphs of a batched call, solved one after another on the lane's
+// stream with the cooperative grid-wide kernels on lane_sms SMs (2 blocks per
+// SM) while the batched kernel, launched with those SMs left free, runs the
+// others.  lane_queue queues them (its device memory stays allocated until
+// lane_finish), lane_finish waits, fills the results and reruns any graph
+// whose hierarchy outgrew its arena or scratch.
+struct LaneBatch {
+  std::vector<BatchItem> items;
+  State *hs = nullptr;  // pinned: the state copies must not block the host
+  char *d = nullptr;
+  double scale = 1.0;
+  ~LaneBatch() {
+    if (hs) cudaFreeHost(hs);
+  }
+};
+
+fiedler_status lane_queue(fiedler_plan *p, LaneBatch &lb, int type) {
+  const size_t tsz = type == 0 ? 8 : 4;
+  const int nbl = p->lane.blocks[type];
+  std::vector<size_t> off(lb.items.size());
+  size_t total = 0;
+  for (size_t i = 0; i < lb.items.size(); i++) {
+    BatchItem &it = lb.items[i];
+    it.arena_b = r256((size_t)(arena_estimate(it.n, it.nnz, tsz, it.wf64, p->opt) * lb.scale));
+    it.scratch_b = r256((size_t)(scratch_estimate(it.n, it.nnz, nbl, p->opt) * lb.scale));
+    off[i] = total;
+    total += r256(sizeof(State)) + it.arena_b + it.scratch_b;
+    if (it.host_in)
+      total += r256(4 * (size_t)(it.n + 1)) + r256(4 * (size_t)std::max<int64_t>(it.nnz, 1)) +
+               r256((it.wf64 ? 8 : 4) * (size_t)std::max<int64_t>(it.nnz, 1));
+    if (it.user_x && !it.user_x_dev) total += r256(8 * (size_t)it.n);
+  }
+  CK(cudaMallocAsync((void **)&lb.d, std::max<size_t>(total, 256), p->lane.stream));
+  if (lb.hs) cudaFreeHost(lb.hs);
+  lb.hs = nullptr;
+  CK(cudaMallocHost((void **)&lb.hs, sizeof(State) * lb.items.size()));
+  const fz::KernelSet &K = p->ks[type];
+  for (size_t i = 0; i < lb.items.size(); i++) {
+    BatchItem &it = lb.items[i];
+    char *base = lb.d + off[i];
+    State *h = &lb.hs[i];
+    memset(h, 0, sizeof(State));
+    fill_opts(h->opt, p->opt, type);
+    h->opt.fault_inject = 0;
+    h->bad_index = LLONG_MAX;
+    h->n0 = (int)it.n;
+    h->nnz0 = (int)it.nnz;
+    h->arena = base + r256(sizeof(State));
+    h->arena_size = it.arena_b;
+    h->scratch = h->arena + it.arena_b;
+    h->scratch_size = it.scratch_b;
+    char *q = h->scratch + it.scratch_b;
+    h->in_rowptr = it.rp;
+    h->in_col = it.ci;
+    h->in_w = it.w;
+    h->in_w_f64 = it.wf64;
+    if (it.host_in) {
+      const size_t rb = r256(4 * (size_t)(it.n + 1)), cb = r256(4 * (size_t)std::max<int64_t>(it.nnz, 1));
+      CK(cudaMemcpyAsync(q, it.rp, 4 * (size_t)(it.n + 1), cudaMemcpyHostToDevice, p->lane.stream));
+      if (it.nnz > 0) {
+        CK(cudaMemcpyAsync(q + rb, it.ci, 4 * (size_t)it.nnz, cudaMemcpyHostToDevice, p->lane.stream));
+        CK(cudaMemcpyAsync(q + rb + cb, it.w, (it.wf64 ? 8 : 4) * (size_t)it.nnz, cudaMemcpyHostToDevice,
+                           p->lane.stream));
+      }
+      h->in_rowptr = (const int *)q;
+      h->in_col = (const int *)(q + rb);
+      h->in_w = q + rb + cb;
+      q += rb + cb + r256((it.wf64 ? 8 : 4) * (size_t)std::max<int64_t>(it.nnz, 1));
+    }
+    h->xout = it.user_x ? (it.user_x_dev ? it.user_x : (double *)q) : nullptr;
+    it.x_off = (size_t)(q - lb.d);
+    h->ipart = p->lane.ipart;
+    h->dpart = p->lane.dpart;
+    CK(cudaMemcpyAsync(base, h, sizeof(State), cudaMemcpyHostToDevice, p->lane.stream));
+    void *args[] = {(void *)&base};
+    CK(cudaLaunchCooperativeKernel(K.grid_setup, dim3(nbl), dim3(fz::kGridThreads), args, 0, p->lane.stream));
+    CK(cudaLaunchKernel(K.cta, dim3(1), dim3(fz::kCtaThreads), args, 0, p->lane.stream));
+    CK(cudaLaunchCooperativeKernel(K.grid_solve, dim3(nbl), dim3(fz::kGridThreads), args, 0, p->lane.stream));
+    CK(cudaMemcpyAsync(h, base, sizeof(State), cudaMemcpyDeviceToHost, p->lane.stream));
+    it.in_off = off[i];
+  }
+  return FIEDLER_OK;
+}
+
+fiedler_status lane_finish(fiedler_plan *p, LaneBatch &lb, int type) {
+  for (int attempt = 0;; attempt++) {
+    CK(cudaStreamSynchronize(p->lane.stream));
+    std::vector<BatchItem> again;
+    for (size_t i = 0; i < lb.items.size(); i++) {
+      BatchItem &it = lb.items[i];
+      const State *h = &lb.hs[i];
+      it.st = h->status;
+      if (needs_rerun(h->status) && attempt < 3) {
+        again.push_back(it);
+        continue;
+      }
+      fiedler_result r{};
+      fiedler_status out = map_status(h->status);
+      if (out == FIEDLER_OK && !h->finalized) out = FIEDLER_ECUDA;
+      if (out == FIEDLER_OK && h->capped) out = FIEDLER_ENOTCONVERGED;
+      if (needs_rerun(h->status)) out = FIEDLER_ENOMEM;
+      r.levels = h->nlevels;
+      r.coarsest_n = h->nlevels > 0 ? h->lv[h->coarsest].n : 0;
+      r.bad_index = h->bad_index == LLONG_MAX ? -1 : h->bad_index;
+      double ns = 0.0;
+      for (int k = 0; k < 2; k++)
+        for (int ph = 0; ph < fz::PH_COUNT; ph++) ns += h->phase_ns[k][ph];
+      r.ms = (float)(ns * 1e-6);
+      if (out == FIEDLER_OK || out == FIEDLER_ENOTCONVERGED) {
+        r.lambda2 = h->lambda;
+        r.residual = h->residual;
+        r.ortho = h->ortho;
+        r.pi_iters_total = h->pi_total;
+        r.gs_sweeps_total = h->gs_total;
+        r.refine_iters = h->refine_total;
+        if (it.user_x && !it.user_x_dev)
+          CK(cudaMemcpy(it.user_x, lb.d + it.x_off, 8 * (size_t)it.n, cudaMemcpyDeviceToHost));
+      }
+      r.x = it.user_x;
+      r.x_on_device = it.user_x_dev;
+      r.status = out;
+      if (it.res) *it.res = r;
+    }
+    CK(cudaFreeAsync(lb.d, p->lane.stream));
+    lb.d = nullptr;
+    if (again.empty()) return FIEDLER_OK;
+    lb.items = again;
+    lb.scale *= 2.0;
+    fiedler_status st = lane_queue(p, lb, type);
+    if (st != FIEDLER_OK) return st;
+  }
+}
+
+}  // namespace
+
 fiedler_status fiedler_solve_batch(fiedler_plan *p, const fiedler_graph *graphs, int count, fiedler_result *results) {
   if (!p || count < 0 || (count > 0 && (!graphs || !results))) return FIEDLER_EINVAL;
   std::lock_guard<std::mutex> ex(p->exec_mu);
@@ -1217,7 +1595,30 @@ fiedler_status fiedler_solve_batch(fiedler_plan *p, const fiedler_graph *graphs,
     c.items.push_back(it);
   }
   if (c.items.empty()) return FIEDLER_OK;
-  return batch_run_sync(p, c);
+  LaneBatch lb;
+  c.reserve_sms = 0;
+  if (p->lane.stream) {  // the large graphs to the lane, queued first so that both run at once
+    std::vector<BatchItem> rest;
+    for (auto &it : c.items) (it.n >= p->opt.lane_min_n ? lb.items : rest).push_back(it);
+    if (!lb.items.empty()) {
+      cudaEvent_t e = nullptr;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      CK(cudaEventRecord(e, p->stream));  // inputs the caller queued on the plan's stream
+      CK(cudaStreamWaitEvent(p->lane.stream, e, 0));
+      cudaEventDestroy(e);
+      fiedler_status st = lane_queue(p, lb, c.type);
+      if (st != FIEDLER_OK) return st;
+      c.items = rest;
+      c.reserve_sms = p->opt.lane_sms;
+    }
+  }
+  fiedler_status st = c.items.empty() ? FIEDLER_OK : batch_run_sync(p, c);
+  if (!lb.items.empty()) {
+    fiedler_status ls = lane_finish(p, lb, c.type);
+    if (st == FIEDLER_OK) st = ls;
+  }
+  c.reserve_sms = 0;
+  return st;
 }
 
 fiedler_status fiedler_plan_autotune(fiedler_plan *p, const fiedler_graph *graphs, int count, fiedler_tuning *out) {
@@ -1400,6 +1801,13 @@ void fiedler_plan_destroy(fiedler_plan *p) {
   if (p->d_state) cudaFree(p->d_state);
   if (p->d_ipart) cudaFree(p->d_ipart);
   if (p->d_dpart) cudaFree(p->d_dpart);
+  if (p->lane.stream) {
+    cudaStreamSynchronize(p->lane.stream);
+    cudaStreamDestroy(p->lane.stream);
+  }
+  if (p->lane.ev) cudaEventDestroy(p->lane.ev);
+  if (p->lane.ipart) cudaFree(p->lane.ipart);
+  if (p->lane.dpart) cudaFree(p->lane.dpart);
   if (p->h_state) cudaFreeHost(p->h_state);
   for (int i = 0; i < 10; i++)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);

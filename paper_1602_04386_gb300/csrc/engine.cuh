@@ -36,6 +36,11 @@
 namespace fz {
 
 #define FZD __device__ __forceinline__
+// the colouring round (run at every setup barrier), the refinement, the
+// V-cycle and Alg. 1's random-order coarsening are real calls: inlined into
+// the kernels beside the rest of the engine they multiply compile time and
+// register pressure (their inner loops stay inline)
+#define FZN __device__ __noinline__
 
 // ---------------------------------------------------------------------------
 // splitmix64 (S. Vigna): output k of the stream seeded with s is
@@ -103,14 +108,23 @@ FZD void best_set(Best &b, uint64_t wk, int u, int v) {
 // the Gram matrix S^T S and the projection S^T L S of the basis S = [x, w, p]
 // (row-major 3 x 3).  The basis is scaled to unit columns, w and then p are
 // dropped when their Cholesky pivot of the scaled Gram matrix falls below
-// kRrPivot (nearly dependent directions), the k x k problem R^-1 H R^-T u =
+// `pivot` (nearly dependent directions), the k x k problem R^-1 H R^-T u =
 // theta u (G = R R^T) is solved by cyclic Jacobi rotations, and the smallest
 // Ritz value is returned with its coefficients c in the unscaled basis (0 for
 // dropped or unused vectors).  Returns a negative value if x alone is left
-// and no step is possible.
-constexpr double kRrPivot = 1e-10;
+// and no step is possible.  The pivot bound follows the accuracy of the sums:
+// with float vectors a direction less than 1e-3 away (in sine) from the span
+// of the others is lost in the rounding of H, and R^-1 would amplify it.
+constexpr double kRrPivot64 = 1e-10;
+constexpr double kRrPivot32 = 1e-6;
+// LOBPCG ends after this many steps in a row without a new lowest Rayleigh
+// quotient (in exact arithmetic every step lowers it).  Not fewer: when
+// lambda_3 lies within ~1% of lambda_2 the iteration can sit a few steps on a
+// lambda_3 plateau, where a float run's descent hides under rounding, before
+// the lambda_2 component takes over
+constexpr int kRefineFlat = 8;
 
-FZD double rr3(const double *G, const double *H, bool use_w, bool use_p, double *c) {
+FZD double rr3(const double *G, const double *H, bool use_w, bool use_p, double *c, double pivot) {
   int act[3], k;
   double D[3], R[3][3], M[3][3], Vv[3][3];
   for (;;) {
@@ -125,7 +139,7 @@ FZD double rr3(const double *G, const double *H, bool use_w, bool use_p, double 
         double sum = G[act[i] * 3 + act[j]] * D[i] * D[j];
         for (int m = 0; m < j; m++) sum -= R[i][m] * R[j][m];
         if (i == j) {
-          if (!(sum > kRrPivot)) {
+          if (!(sum > pivot)) {
             bad = i;
             break;
           }
@@ -683,6 +697,8 @@ struct Eng {
   int cur_level;    // level being worked on (profile)
   // control flow, identical in every thread
   int nlevels, setup_done, coarsest, coarsest_solved, solved, finalized, refined;
+  // grid form only: block 0 working alone (barriers and sums within the block)
+  bool local_;
 
   // ---- infrastructure ------------------------------------------------------
   FZD void init(State *s) {
@@ -707,6 +723,7 @@ struct Eng {
     t_last = 0;
     ngen = 0;
     cur_level = 0;
+    local_ = false;
     if (threadIdx.x == 0) jps().active = 0;
     if (bid == 0) {
       for (int i = threadIdx.x; i < 2 * PH_COUNT + kMaxLevels * PH_COUNT; i += blockDim.x) sh_prof()[i] = 0.0;
@@ -793,7 +810,7 @@ struct Eng {
   }
 
   FZD bool barrier() {
-    if (!GRID) return __syncthreads_and(status() == 0);
+    if (!GRID || local_) return __syncthreads_and(status() == 0);
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -855,7 +872,7 @@ struct Eng {
   FZD bool grid_ired(IRed &r, long long *pre_a = nullptr, long long *pre_b = nullptr) {
     block_ired(r);
     long long pa = 0, pb = 0;
-    if (GRID) {
+    if (GRID && !local_) {
       IRed *part = S->ipart + rb * kMaxBlocks;
       if (threadIdx.x == 0) part[bid] = r;
       if (!(PUMP ? sync_p() : sync())) return false;
@@ -909,7 +926,7 @@ struct Eng {
   template <int K>
   FZD bool grid_dsum(double (&v)[K]) {
     block_dsum<K>(v);
-    if (GRID) {
+    if (GRID && !local_) {
       double *part = S->dpart + (size_t)rb * kMaxBlocks * kDSum;
       if (threadIdx.x == 0)
 #pragma unroll
@@ -964,7 +981,7 @@ struct Eng {
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = sh[32 * K + k];
     __syncthreads();
-    if (GRID) {
+    if (GRID && !local_) {
       double *part = S->dpart + (size_t)rb * kMaxBlocks * kDSum;
       if (threadIdx.x == 0)
 #pragma unroll
@@ -1232,7 +1249,7 @@ struct Eng {
     return true;
   }
 
-  FZD void jp_round() {
+  FZN void jp_round() {
     JPState &jp = jps();
     const Level *L = &S->lv[jp.l];
     const int *rp = L->rowptr, *ci = L->col;
@@ -1393,7 +1410,7 @@ struct Eng {
     }
   }
 
-  FZD void jp_after() {
+  FZN void jp_after() {
     JPState &jp = jps();
     const int r = jp.r, l = jp.l;
     const int left = *(volatile int *)&S->jp_cnt[(r + 1) % 3];
@@ -1825,7 +1842,7 @@ struct Eng {
   // belongs to first(u)'s aggregate; joins are followed by pointer jumping
   // (chains of m end in a founder: m has no cycles longer than two), and the
   // founders are numbered in visit order by a bucket sort of their keys.
-  FZD bool hec_paper(int l, int &nc_out, GalerkinScratch &G) {
+  FZN bool hec_paper(int l, int &nc_out, GalerkinScratch &G) {
     cur_level = l;
     Level *L = &S->lv[l];
     const int n = L->n;
@@ -1962,6 +1979,8 @@ struct Eng {
       }
       if (lead()) bst[B] = (int)nc;
     }
+    // every block has read its chunk of the counts before any clears them
+    if (!sync_p()) return false;
     for (int b = tid; b < B; b += nthr) bcnt[b] = 0;
     if (!sync_p()) return false;
     for (int u = tid; u < n; u += nthr)
@@ -2171,6 +2190,19 @@ struct Eng {
       }
     }
     if (!sync_p()) return false;
+    // the V-cycle preconditioner of the refinement restricts through these
+    // sorted member lists: kept in the arena
+    if (S->opt.refine == 1 && S->opt.refine_precond == 1) {
+      int *mptr = (int *)aalloc(4ull * (nc + 1));
+      int *mem = (int *)aalloc(4ull * n);
+      if (!mptr || !mem) return false;
+      for (long long I = tid; I <= nc; I += nthr) mptr[I] = G.aggptr[I];
+      for (int k = tid; k < n; k += nthr) mem[k] = G.members[k];
+      if (lead()) {
+        L->mptr = mptr;
+        L->mem = mem;
+      }
+    }
     // G5: cross entries into their aggregate's segment, key = (J, slot); a
     // heavy row's slots are handed out in entry order by ballots over chunks
     for (int v = tid; v < n; v += nthr) {
@@ -2898,7 +2930,7 @@ struct Eng {
   // ---- finest-level Krylov refinement (Sec. 4's Krylov smoother) ----------
   // Runs in place of the finest level's power iteration, after its
   // Gauss-Seidel sweeps, until ||L x - theta x|| <= refine_tol theta ||x||.
-  FZD bool refine() {
+  FZN bool refine() {
     cur_level = 0;
     const int n = S->lv[0].n, nnz = S->lv[0].nnz;
     if (GRID && vdbl(n, nnz) && sizeof(T) != 8) {  // see smooth()
@@ -2915,7 +2947,7 @@ struct Eng {
   // thread's view of the shared array h: per warp by xor trees, the block's
   // warps and (grid form) the blocks' partials in fixed order
   template <class V>
-  FZD bool basis_dots(const V *Q, size_t ldq, const V *U, int n, int k, double *h) {
+  FZN bool basis_dots(const V *Q, size_t ldq, const V *U, int n, int k, double *h) {
     double *wp = reinterpret_cast<double *>(sh_raw());  // [warps][kMaxBasis + 1]
     constexpr int LD = kMaxBasis + 1;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -2933,7 +2965,7 @@ struct Eng {
       h[t] = a;
     }
     __syncthreads();
-    if (GRID) {
+    if (GRID && !local_) {
       double *part = S->dpart + (size_t)rb * kMaxBlocks * kDSum;
       for (int t = threadIdx.x; t < k; t += blockDim.x) part[bid * kDSum + t] = h[t];
       if (!sync()) return false;
@@ -2956,7 +2988,7 @@ struct Eng {
   // Q_0..Q_m (rows of n values), work vector U; the tridiagonal problem is
   // solved by one thread.
   template <class V>
-  FZD bool lanczos_v() {
+  FZN bool lanczos_v() {
     Level *L = &S->lv[0];
     const int n = L->n, nnz = L->nnz;
     const int m = S->opt.lanczos_basis;
@@ -3115,6 +3147,204 @@ struct Eng {
     });
   }
 
+  // ---- V-cycle preconditioner of the LOBPCG refinement ---------------------
+  // One V-cycle of the cascade's own hierarchy on L e = r: per level one
+  // forward Gauss-Seidel sweep from e = 0 (colour classes ascending; a class
+  // has no internal edges, so rows update in place in any order), the
+  // residual summed over each aggregate (members ascending, FP64 sums) as the
+  // next level's right-hand side, 20 sweeps and the mean removed on the
+  // coarsest level, the correction added to every member, one backward sweep
+  // (classes descending).  Level l's vectors vb (rhs), ve (correction), vt
+  // (residual) have the level's value type.
+  template <class F>
+  FZD void with_ltype(int l, F f) {
+    if (vdbl(S->lv[l].n, S->lv[l].nnz)) f((double)0);
+    else f((T)0);
+  }
+
+  template <class V>
+  FZD void vc_class(const Level *L, int c, const V *b, V *e) {
+    const int C = L->ncolors, n = L->n;
+    const int *cst = L->colstart, *srp = L->srowptr, *scol = L->scol;
+    const V *sw = (const V *)L->sw;
+    const int nl = cst[C], cs = cst[c], ce = cst[c + 1], hs = cst[C + c], he = cst[C + c + 1];
+    for (int i = cs + tid; i < ce; i += nthr) {
+      V num = b[i], dsum = (V)0;
+      const int e1 = srp[i + 1];
+      for (int k = srp[i]; k < e1; k++) {
+        const V wv = sw[k];
+        num += wv * e[scol[k]];
+        dsum += wv;
+      }
+      e[i] = num / dsum;
+    }
+    const int lane = threadIdx.x & 31, gw = tid >> 5, nwarp = nthr >> 5;
+    with_group<GRID>(heavy_group(srp, nl, n), [&](auto gs) {
+      constexpr int G = decltype(gs)::value, GW = 32 / G;
+      const int gl = lane & (G - 1), gi = lane / G;
+      for (int base = hs + gw * GW; base < he; base += nwarp * GW) {
+        const int i = base + gi;
+        V num = (V)0, dsum = (V)0;
+        if (i < he)
+          group_row<G>(srp[i], srp[i + 1], scol, sw, [&](int j, V wv) {
+            num += wv * e[j];
+            dsum += wv;
+          });
+        num = group_sum<G>(num);
+        dsum = group_sum<G>(dsum);
+        if (gl == 0 && i < he) e[i] = (b[i] + num) / dsum;
+      }
+    });
+  }
+
+  template <class V>
+  FZN bool vc_sweeps(int l, bool forward, bool zero_first, int count) {
+    const Level *L = &S->lv[l];
+    const V *b = (const V *)L->vb;
+    V *e = (V *)L->ve;
+    const int C = L->ncolors;
+    if (zero_first) {
+      for (int i = tid; i < L->n; i += nthr) e[i] = (V)0;
+      if (!sync()) return false;
+    }
+    for (int k = 0; k < count; k++)
+      for (int q = 0; q < C; q++) {
+        vc_class<V>(L, forward ? q : C - 1 - q, b, e);
+        if (!sync()) return false;
+      }
+    return true;
+  }
+
+  template <class V>
+  FZN bool vc_resid(int l) {
+    const Level *L = &S->lv[l];
+    const V *b = (const V *)L->vb;
+    V *t = (V *)L->vt;
+    lap_rows<V>(L, (const V *)L->ve, [&](int i, V lv, V dv) { t[i] = b[i] - lv; });
+    return sync();
+  }
+
+  template <class VF, class VC>
+  FZN bool vc_restrict(int l) {
+    const Level *F = &S->lv[l];
+    const Level *Cl = &S->lv[l + 1];
+    const int nc = Cl->n;
+    const int *mptr = F->mptr, *mem = F->mem, *ipf = F->iperm, *ipc = Cl->iperm;
+    const VF *t = (const VF *)F->vt;
+    VC *bc = (VC *)Cl->vb;
+    for (int I = tid; I < nc; I += nthr) {
+      double s = 0.0;
+      for (int k = mptr[I]; k < mptr[I + 1]; k++) s += (double)t[ipf[mem[k]]];
+      bc[ipc[I]] = (VC)s;
+    }
+    return sync();
+  }
+
+  template <class V>
+  FZN bool vc_coarsest(int J) {
+    const Level *L = &S->lv[J];
+    if (!vc_sweeps<V>(J, true, true, 20)) return false;
+    V *e = (V *)L->ve;
+    double acc[1] = {0.0};
+    for (int i = tid; i < L->n; i += nthr) acc[0] += (double)e[i];
+    if (!grid_dsum<1>(acc)) return false;
+    const V mu = (V)(acc[0] / (double)L->n);
+    for (int i = tid; i < L->n; i += nthr) e[i] = e[i] - mu;
+    return sync();
+  }
+
+  template <class VF, class VC>
+  FZN bool vc_prolong(int l) {
+    const Level *F = &S->lv[l];
+    const Level *Cl = &S->lv[l + 1];
+    VF *ef = (VF *)F->ve;
+    const VC *ec = (const VC *)Cl->ve;
+    const int *sagg = F->sagg;
+    for (int k = tid; k < F->n; k += nthr) ef[k] = ef[k] + (VF)ec[sagg[k]];
+    return sync();
+  }
+
+  // down-sweep over levels [a, b): pre-smoothing, residual, restriction to l + 1
+  FZD bool vc_down(int a, int b) {
+    bool ok = true;
+    for (int l = a; l < b && ok; l++)
+      with_ltype(l, [&](auto tf) {
+        using VF = decltype(tf);
+        ok = vc_sweeps<VF>(l, true, true, 1) && vc_resid<VF>(l);
+        if (ok)
+          with_ltype(l + 1, [&](auto tc) {
+            using VC = decltype(tc);
+            ok = vc_restrict<VF, VC>(l);
+          });
+      });
+    return ok;
+  }
+  // up-sweep over levels a down to b: prolongation from l + 1, post-smoothing
+  FZD bool vc_up(int a, int b) {
+    bool ok = true;
+    for (int l = a; l >= b && ok; l--)
+      with_ltype(l, [&](auto tf) {
+        using VF = decltype(tf);
+        with_ltype(l + 1, [&](auto tc) {
+          using VC = decltype(tc);
+          ok = vc_prolong<VF, VC>(l);
+        });
+        if (ok) ok = vc_sweeps<VF>(l, false, false, 1);
+      });
+    return ok;
+  }
+  FZD bool vc_bottom(int J) {
+    bool ok = true;
+    with_ltype(J, [&](auto t) {
+      using V = decltype(t);
+      ok = vc_coarsest<V>(J);
+    });
+    return ok;
+  }
+
+  // e_0 = V(b_0): the right-hand side in level 0's vb, the result in its ve.
+  // In the grid form the small levels (those the one-block engine sets up)
+  // are cycled by block 0 alone with block barriers, while the other blocks
+  // wait at one grid barrier: there a grid barrier per colour pass would cost
+  // far more than the levels' work.
+  FZN bool vcycle() {
+    const int J = nlevels - 1;
+    if (!GRID) return vc_down(0, J) && vc_bottom(J) && vc_up(J - 1, 0);
+    int ls = 0;
+    while (ls < J && !small(S->lv[ls].n, S->lv[ls].nnz)) ls++;
+    if (!vc_down(0, ls)) return false;
+    if (bid == 0) {
+      const int stid = tid, snthr = nthr, snb = nb;
+      local_ = true;
+      tid = threadIdx.x;
+      nthr = blockDim.x;
+      nb = 1;
+      vc_down(ls, J) && vc_bottom(J) && vc_up(J - 1, ls);
+      local_ = false;
+      tid = stid;
+      nthr = snthr;
+      nb = snb;
+    }
+    if (!sync()) return false;
+    return vc_up(ls - 1, 0);
+  }
+
+  // the V-cycle's per-level vectors, from the arena
+  FZN bool vc_alloc() {
+    for (int l = 0; l < nlevels; l++) {
+      Level *L = &S->lv[l];
+      const unsigned long long vs = vdbl(L->n, L->nnz) ? 8ull : sizeof(T);
+      void *b = aalloc(vs * L->n), *e = aalloc(vs * L->n), *t = aalloc(vs * L->n);
+      if (!b || !e || !t) return false;
+      if (lead()) {
+        L->vb = b;
+        L->ve = e;
+        L->vt = t;
+      }
+    }
+    return sync();
+  }
+
   // LOBPCG (Knyazev 2001), one vector, on 1-perp with the preconditioner
   // D^-1.  Iterate X, preconditioned residual W = D^-1 (L X - theta X), search
   // direction P; the means of X, W and P are removed lazily (x = X - mu_x ...;
@@ -3123,13 +3353,14 @@ struct Eng {
   // lets the iteration diverge).  Per iteration: a matvec pass (L X, L P, the
   // Rayleigh quotient and residual sums), a pass forming W, a matvec pass L W
   // with the Gram sums of [x, w, p], one FP64 Rayleigh-Ritz step, an update
-  // pass.  Stops when ||L x - theta x|| <= refine_tol theta ||x||, when theta
-  // did not decrease in a step (each Rayleigh-Ritz step lowers it in exact
-  // arithmetic: this is the rounding floor of the value type; float iterates
-  // reach it near a residual of 1e-3 theta with lambda_2 exact to ~1e-8), or
-  // at refine_max_iters.
+  // pass.  Stops when ||L x - theta x|| <= refine_tol theta ||x||, after
+  // kRefineFlat steps in a row without a new lowest theta (each Rayleigh-Ritz
+  // step lowers it in exact arithmetic: this is the rounding floor of the
+  // value type; float iterates reach it near a residual of 1e-3 theta with
+  // lambda_2 exact to ~1e-8; such a step also restarts without p), or at
+  // refine_max_iters.
   template <class V>
-  FZD bool lobpcg_v() {
+  FZN bool lobpcg_v() {
     Level *L = &S->lv[0];
     const int n = L->n, nnz = L->nnz;
     V *A = (V *)L->x;
@@ -3141,6 +3372,9 @@ struct Eng {
     V *LP = (V *)aalloc(sizeof(V) * (size_t)n);
     V *DI = (V *)aalloc(sizeof(V) * (size_t)n);
     if (!X || !LX || !W || !LW || !P || !LP || !DI) return false;
+    const bool vc = S->opt.refine_precond == 1;
+    if (vc && !vc_alloc()) return false;
+    V *VB = (V *)L->vb;  // level 0's V-cycle right-hand side (vc only)
     const double tol = S->opt.refine_tol;
     const int kmax = S->opt.refine_max_iters;
     const double inv_n = 1.0 / (double)n;
@@ -3151,9 +3385,9 @@ struct Eng {
       for (int i = tid; i < n; i += nthr) X[i] = (A[i] - muT) * sT;
       if (!sync()) return false;
     }
-    double mux = 0.0, mup = 0.0, theta_prev = 0.0;
+    double mux = 0.0, mup = 0.0, theta_best = 0.0;
     bool pvalid = false;
-    int iters = 0, capped = 0;
+    int iters = 0, capped = 0, flat = 0;
     for (;;) {
       // L X and L P afresh; sums for theta and the means (X's stored mean is
       // the update's rounding only: it is measured here, and L 1 = 0)
@@ -3175,28 +3409,52 @@ struct Eng {
       mux = acc[2] * inv_n;
       mup = acc[3] * inv_n;
       const double xx = acc[0] - acc[2] * mux, theta = acc[1] / xx;
-      // residual r = L x - theta x (its norm for the stop rule) and W = D^-1 r,
-      // whose mean mu_w is removed where W is read
+      // residual r = L x - theta x (its norm for the stop rule) and the
+      // preconditioned W = D^-1 r, or r as the V-cycle's right-hand side;
+      // W's mean mu_w is removed where W is read
       double racc[2] = {0.0, 0.0};
       {
         const V mx = (V)mux, th = (V)theta;
         for (int i = tid; i < n; i += nthr) {
           const V r = LX[i] - th * (X[i] - mx);
-          const V wv = DI[i] * r;
-          W[i] = wv;
           racc[0] += (double)r * (double)r;
-          racc[1] += (double)wv;
+          if (vc) {
+            VB[i] = r;
+          } else {
+            const V wv = DI[i] * r;
+            W[i] = wv;
+            racc[1] += (double)wv;
+          }
         }
       }
       if (!grid_wsum<2>(racc)) return false;
-      const double muw = racc[1] * inv_n;
+      double muw = racc[1] * inv_n;
       if (racc[0] <= tol * tol * theta * theta * xx) break;
-      if (iters > 0 && theta >= theta_prev) break;  // no descent: the rounding floor
+      if (iters == 0 || theta < theta_best) {
+        theta_best = theta;
+        flat = 0;
+      } else {
+        // no new lowest Rayleigh quotient (only rounding causes it): restart
+        // without p; kRefineFlat such steps in a row are the rounding floor
+        pvalid = false;
+        if (++flat >= kRefineFlat) break;
+      }
       if (iters >= kmax) {
         capped = 1;
         break;
       }
-      theta_prev = theta;
+      if (vc) {  // W = V(r)
+        if (!vcycle()) return false;
+        const V *E = (const V *)L->ve;
+        double wacc[1] = {0.0};
+        for (int i = tid; i < n; i += nthr) {
+          const V wv = E[i];
+          W[i] = wv;
+          wacc[0] += (double)wv;
+        }
+        if (!grid_wsum<1>(wacc)) return false;
+        muw = wacc[0] * inv_n;
+      }
       // L W and the Gram sums of [x, w, p]
       double g[12];
 #pragma unroll
@@ -3207,18 +3465,21 @@ struct Eng {
           LW[i] = lv;
           const double xh = (double)(X[i] - mx), wh = (double)(W[i] - mw), lx = (double)LX[i];
           const double lw = (double)lv;
+          // x^T L w is taken as (L x)^T w: L x of the smooth iterate comes out of
+          // the difference form nearly exact, while a float L w carries an error
+          // of eps ||L|| ||w||, large beside x^T L w once the residual is small
           g[0] += xh * xh;
           g[1] += xh * wh;
           g[3] += wh * wh;
           g[6] += xh * lx;
-          g[7] += xh * lw;
+          g[7] += lx * wh;
           g[9] += wh * lw;
           if (pvalid) {
             const double ph = (double)(P[i] - mp), lp = (double)LP[i];
             g[2] += xh * ph;
             g[4] += wh * ph;
             g[5] += ph * ph;
-            g[8] += xh * lp;
+            g[8] += lx * ph;
             g[10] += wh * lp;
             g[11] += ph * lp;
           }
@@ -3231,7 +3492,9 @@ struct Eng {
         const double G[9] = {g[0], g[1], g[2], g[1], g[3], g[4], g[2], g[4], g[5]};
         const double H[9] = {g[6], g[7], g[8], g[7], g[9], g[10], g[8], g[10], g[11]};
         double c[3];
-        const double th = rr3(G, H, true, pvalid, c);
+        const double piv = sizeof(V) == 4 ? kRrPivot32 : kRrPivot64;
+        double th = rr3(G, H, true, pvalid, c, piv);
+        if (!(th > 0.0) && pvalid) th = rr3(G, H, true, false, c, piv);  // again without p
         double nx = 0.0, np = 0.0;
         if (th > 0.0)
           for (int a = 0; a < 3; a++)

@@ -1,17 +1,14 @@
-// engine_f64.cu -- double instantiation of the level engine.
-#include "engine.cuh"
+// engine_f64.cu -- double instantiation of the level engine: the kernel table (the
+// kernels themselves are in engine_f64_setup.cu, engine_f64_solve.cu,
+// engine_f64_cta.cu and engine_batch*_f64.cu).
 #include "kernels.h"
 
 namespace fz {
 
-__global__ void __launch_bounds__(kGridThreads, 2) fz_grid_setup_f64(State *S) { engine_entry<double, true>(S, 0); }
-__global__ void __launch_bounds__(kGridThreads, 2) fz_grid_solve_f64(State *S) { engine_entry<double, true>(S, 2); }
-__global__ void __launch_bounds__(kCtaThreads, 1) fz_cta_f64(State *S) { engine_entry<double, false>(S, 1); }
-
 void kernels_f64(KernelSet *k) {
-  k->grid_setup = (const void *)fz_grid_setup_f64;
-  k->grid_solve = (const void *)fz_grid_solve_f64;
-  k->cta = (const void *)fz_cta_f64;
+  grid_setup_kernel_f64(k);
+  grid_solve_kernel_f64(k);
+  cta_kernel_f64(k);
   k->names[0] = "fz_grid_setup_f64";
   k->names[1] = "fz_cta_f64";
   k->names[2] = "fz_grid_solve_f64";

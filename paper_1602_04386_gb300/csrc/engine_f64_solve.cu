@@ -1,0 +1,13 @@
+// engine_f64_solve.cu -- double instantiation of the level engine: the grid solve kernel.
+// Each kernel of the single-graph solve has a translation unit of its own, so
+// that they compile in parallel.
+#include "engine.cuh"
+#include "kernels.h"
+
+namespace fz {
+
+__global__ void __launch_bounds__(kGridThreads, 2) fz_grid_solve_f64(State *S) { engine_entry<double, true>(S, 2); }
+
+void grid_solve_kernel_f64(KernelSet *k) { k->grid_solve = (const void *)fz_grid_solve_f64; }
+
+}  // namespace fz

@@ -45,6 +45,8 @@ struct Opts {
   int refine_max_iters;
   int lanczos_basis;
   int hec_mode;              // 0: locally dominant matching; 1: Alg. 1's random-order greedy
+  int refine_precond;        // LOBPCG preconditioner: 0 D^-1, 1 V-cycle of the hierarchy
+  int pad_opt;
   double refine_tol;
   double stall_ratio;
   double pi_cos_tol;
@@ -76,6 +78,11 @@ struct Level {
   // iterate: x (or y) with a lazy affine map xhat = (x - mu) * s
   void *x, *y;
   double mu, s;
+  // V-cycle preconditioner: members of each aggregate (graph numbering,
+  // ascending; kept from the Galerkin step) and the level's right-hand side,
+  // correction and residual vectors (value type of the level)
+  int *mptr, *mem;
+  void *vb, *ve, *vt;
   // counters
   int match_rounds, color_rounds, gs_sweeps, pi_iters, capped;
   int refine_iters;

@@ -16,6 +16,12 @@ struct KernelSet {
 constexpr int kBatchThreads[3] = {512, 256, 128};
 void kernels_f32(KernelSet *k);
 void kernels_f64(KernelSet *k);
+void grid_setup_kernel_f32(KernelSet *k);
+void grid_solve_kernel_f32(KernelSet *k);
+void cta_kernel_f32(KernelSet *k);
+void grid_setup_kernel_f64(KernelSet *k);
+void grid_solve_kernel_f64(KernelSet *k);
+void cta_kernel_f64(KernelSet *k);
 void batch_kernel512_f32(KernelSet *k);
 void batch_kernel256_f32(KernelSet *k);
 void batch_kernel128_f32(KernelSet *k);

@@ -56,13 +56,13 @@ size_t scratch_bytes(int64_t n, int64_t nnz, int hec_mode) {
 
 // hierarchy bound: the fine level plus coarse levels of at most 2n vertices and
 // 2 nnz entries in total (the same bound the plan-owned arena starts from)
-size_t arena_bytes(int64_t n, int64_t nnz, size_t tsz, bool wf64, int refine, int basis) {
+size_t arena_bytes(int64_t n, int64_t nnz, size_t tsz, bool wf64, int refine, int basis, int precond) {
   double l0 = 4.0 * (n + 1) + (4.0 + (wf64 ? 8.0 : 4.0)) * nnz + 8.0 * n + 12.0 * n + 8.0 * n +
               4.0 * (fz::kMaxColors + 1) + 4.0 * (n + 1) + (4.0 + tsz) * nnz + (2.0 * tsz + 4.0) * n;
   double lc = 2.0 * (4.0 * n + 16.0 * nnz + 8.0 * n + 12.0 * n + 8.0 * n + 4.0 * n + (4.0 + tsz) * nnz +
                      (2.0 * tsz + 4.0) * n) +
               fz::kMaxLevels * 4.0 * (fz::kMaxColors + 1) + fz::kMaxLevels * 24.0 * 256.0;
-  return round256((size_t)(l0 + lc + fz::refine_bytes(n, tsz, refine, basis)));
+  return round256((size_t)(l0 + lc + fz::refine_bytes(n, tsz, refine, basis, precond)));
 }
 
 fiedler_status status_of(int st) {
@@ -107,7 +107,7 @@ extern "C" fiedler_status fiedler_solve_noalloc(const fiedler_options *opts, con
   // fixed layout: state | arena | scratch; larger problems are refused up front
   const size_t state_b = round256(sizeof(fz::State));
   size_t scratch_b = scratch_bytes(g->n, g->nnz, o.hec_mode);
-  const size_t need = state_b + arena_bytes(g->n, g->nnz, tsz, wf64, o.refine, o.lanczos_basis) + scratch_b;
+  const size_t need = state_b + arena_bytes(g->n, g->nnz, tsz, wf64, o.refine, o.lanczos_basis, o.refine_precond) + scratch_b;
   if (need > kNoAllocBytes) return refuse(res, FIEDLER_ENOTSUP);
   // the plan's scratch keeps 1 MiB of slack; give it here too when the array has room
   scratch_b += std::min(kScratchSlack, (kNoAllocBytes - need) & ~(size_t)255u);

@@ -42,6 +42,8 @@ FIEDLER_REFINE_LOBPCG = 1
 FIEDLER_REFINE_LANCZOS = 2
 FIEDLER_HEC_DOMINANT = 0
 FIEDLER_HEC_PAPER = 1
+FIEDLER_PRECOND_DEGREE = 0
+FIEDLER_PRECOND_VCYCLE = 1
 
 #: exported symbols declared in include/fiedler.h
 SYMBOLS = (
@@ -50,6 +52,7 @@ SYMBOLS = (
     "fiedler_plan_num_levels", "fiedler_plan_level_info", "fiedler_plan_copy_level",
     "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc",
     "fiedler_solve_batch", "fiedler_plan_serving_stats", "fiedler_plan_autotune", "fiedler_poll_any",
+    "fiedler_partition",
 )
 
 
@@ -80,6 +83,9 @@ class fiedler_options(C.Structure):
         ("refine_tol", C.c_double),
         ("lanczos_basis", C.c_int),
         ("hec_mode", C.c_int),
+        ("refine_precond", C.c_int),
+        ("lane_sms", C.c_int),
+        ("lane_min_n", C.c_int),
     ]
 
 
@@ -127,6 +133,15 @@ class fiedler_level_info(C.Structure):
         ("last_cos", C.c_double),
         ("phase_ms", C.c_float * 16),
         ("refine_iters", C.c_int),
+    ]
+
+
+class fiedler_partition_info(C.Structure):
+    _fields_ = [
+        ("parts", C.c_int),
+        ("solves", C.c_int),
+        ("component_splits", C.c_int),
+        ("ms", C.c_float),
     ]
 
 
@@ -211,6 +226,8 @@ def load():
         L.fiedler_plan_serving_stats.argtypes = [vp, C.POINTER(fiedler_serving_stats)]
         L.fiedler_plan_autotune.argtypes = [vp, C.POINTER(fiedler_graph), C.c_int, C.POINTER(fiedler_tuning)]
         L.fiedler_poll_any.argtypes = [vp, C.POINTER(C.c_uint64), C.c_int, C.c_int, C.POINTER(C.c_int)]
+        L.fiedler_partition.argtypes = [vp, C.POINTER(fiedler_graph), C.c_int, C.c_void_p, C.c_int,
+                                        C.POINTER(fiedler_partition_info)]
         for f in ("fiedler_plan_create", "fiedler_solve", "fiedler_batch_submit", "fiedler_poll", "fiedler_cancel",
                   "fiedler_plan_num_levels", "fiedler_plan_level_info", "fiedler_plan_copy_level",
                   "fiedler_plan_set_profiling", "fiedler_plan_get_profile", "fiedler_solve_noalloc",
@@ -245,6 +262,12 @@ def fiedler_batch_submit(plan, graph: fiedler_graph):
 
 def fiedler_poll(plan, ticket: int, timeout_ms: int, result: fiedler_result) -> int:
     return load().fiedler_poll(plan, ticket, timeout_ms, C.byref(result))
+
+
+def fiedler_partition(plan, graph: fiedler_graph, parts: int, labels_ptr, labels_on_device: int):
+    info = fiedler_partition_info()
+    st = load().fiedler_partition(plan, C.byref(graph), parts, labels_ptr, labels_on_device, C.byref(info))
+    return st, info
 
 
 def fiedler_poll_any(plan, max_count: int, timeout_ms: int):
@@ -451,6 +474,17 @@ class Plan:
         out["w"] = out["w"][:m]
         out["info"] = info
         return out
+
+    def partition(self, g, parts, on_device=True):
+        """Recursive spectral bisection of inputs.CSR g into `parts` parts;
+        returns (labels as numpy int32, fiedler_partition_info)."""
+        gs, keep = device_graph(g) if on_device else host_graph(g)
+        labels = np.zeros(g.n, np.int32)
+        st, info = fiedler_partition(self.h, gs, parts, labels.ctypes.data, 0)
+        del keep
+        if st != FIEDLER_OK:
+            raise FiedlerError(st, "fiedler_partition")
+        return labels, info
 
     def set_profiling(self, on=True):
         fiedler_plan_set_profiling(self.h, 1 if on else 0)

@@ -125,7 +125,7 @@ def test_fp32_free_running_knn_within_1e5(npts, seed):
 @pytest.mark.parametrize("name", ["grid128x96w", "knn8000"])
 def test_fp32_angle_against_tight_oracle(name):
     """FP32 vector against a tightly converged FP64 oracle vector: 1 - |cos| <=
-    1e-6 (the benchmark spec's angle gate) on non-degenerate graphs."""
+    1e-6 on graphs whose lambda_2 is well separated from lambda_3."""
     g = {"grid128x96w": lambda: inputs.grid(128, 96, "uniform", seed=3),
          "knn8000": lambda: inputs.knn_mixture(8000, seed=5)}[name]()
     tight = oracle.solve(g, refine=LOBPCG, refine_tol=1e-9, refine_max_iters=200000)
@@ -165,3 +165,53 @@ def test_batched_refine_equals_alone():
             a = q.solve(g)
         assert rb.status == a.status == fiedler.FIEDLER_OK
         assert rb.lambda2 == a.lambda2 and np.array_equal(rb.x, a.x)
+
+
+LANCZOS = 2
+
+
+@pytest.mark.parametrize("name", ["grid90x61w", "rmat10", "path300"])
+@pytest.mark.parametrize("precision,tol", [(FP64, 1e-10), (FP32, 1e-5)])
+def test_lanczos_replay_parity(name, precision, tol):
+    """Restarted Lanczos (Sec. 4's named smoother) on the finest level: the
+    oracle replayed with the GPU's counts (power iteration per level, Lanczos
+    matvecs) gives the same lambda_2."""
+    g = GRAPHS[name]()
+    with fiedler.Plan(precision=precision, refine=LANCZOS, refine_max_iters=20000) as p:
+        r = p.solve(g)
+        assert r.status == fiedler.FIEDLER_OK, r
+        counts = [p.level_info(l).pi_iters for l in range(p.num_levels)]
+        rit = p.level_info(0).refine_iters
+    assert rit > 0 and counts[0] == 0
+    ref = oracle.solve(g, forced_pi=counts, refine=LANCZOS, refine_forced=rit)
+    assert ref.status == 0 and ref.refine_iters == rit
+    assert abs(r.lambda2 - ref.lam) <= tol * ref.lam, (r.lambda2, ref.lam)
+    if precision == FP64:
+        assert np.abs(r.x - ref.x(g.n)).max() <= 1e-7
+
+
+@pytest.mark.parametrize("name", ["grid90x61w", "rmat13", "knn20k"])
+@pytest.mark.parametrize("precision,tol", [(FP64, 1e-10), (FP32, 1e-5)])
+def test_lobpcg_degree_preconditioner_replay(name, precision, tol):
+    g = GRAPHS[name]()
+    with fiedler.Plan(precision=precision, refine=LOBPCG, refine_precond=0) as p:
+        r = p.solve(g)
+        assert r.status == fiedler.FIEDLER_OK, r
+        counts = [p.level_info(l).pi_iters for l in range(p.num_levels)]
+        rit = p.level_info(0).refine_iters
+    ref = oracle.solve(g, forced_pi=counts, refine=LOBPCG, refine_precond=0, refine_forced=rit)
+    assert abs(r.lambda2 - ref.lam) <= tol * ref.lam, (r.lambda2, ref.lam)
+
+
+def test_vcycle_preconditioner_cuts_steps_on_the_gpu():
+    """On a weighted grid the V-cycle preconditioner needs far fewer LOBPCG
+    steps than D^-1, and both reach the same lambda_2."""
+    g = GRAPHS["grid256x192w"]()
+    out = {}
+    for pre in (0, 1):
+        with fiedler.Plan(precision=FP64, refine=LOBPCG, refine_precond=pre, refine_max_iters=20000) as p:
+            r = p.solve(g)
+            assert r.status == fiedler.FIEDLER_OK
+            out[pre] = (r.refine_iters, r.lambda2)
+    assert out[1][0] * 5 < out[0][0]
+    assert abs(out[0][1] - out[1][1]) <= 1e-6 * out[1][1]
