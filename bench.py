@@ -62,7 +62,8 @@ def measured_peaks():
 
 # the files that define the single-graph kernels ncu measured (host code and
 # the other kernels' translation units do not change them)
-ENGINE_SOURCES = ("engine.cuh", "fz_state.h", "kernels.h", "engine_f32.cu", "engine_f64.cu")
+ENGINE_SOURCES = ("engine.cuh", "fz_state.h", "kernels.h", "engine_f32_setup.cu", "engine_f32_cta.cu",
+                  "engine_f32_solve.cu")
 
 
 def engine_source_hash():
@@ -441,7 +442,7 @@ def configs_leg(stream, dev, steps=5, warmup=2):
 SERVE = dict(rate=2000.0, seconds=3.0, pool=24, nmin=1e3, nmax=2e6, seed=inputs.BASE_SEED + 5)
 
 
-def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None):
+def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None, **plan_opts):
     """The serving form: a Poisson stream of requests at `rate` per second for
     `seconds`, each a graph drawn uniformly from the pool (device-resident
     inputs, copied by fiedler_batch_submit), submitted at its arrival time and
@@ -462,7 +463,7 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None)
     dgs = [fiedler.device_graph(g, dev) for g in pool]
     torch.cuda.empty_cache()  # earlier legs' cached blocks back to the device
     plan = fiedler.Plan(stream=stream.cuda_stream, max_batch=256, hbm_budget_bytes=200 << 30,
-                        queue_budget_bytes=8 << 30)
+                        queue_budget_bytes=8 << 30, **plan_opts)
     tune = dgs[:16]  # the pool's smaller two thirds (log-spaced sizes up to ~1e5 points), repeated
     tsample = (fiedler.fiedler_graph * len(tune))()
     for k, (gs, _) in enumerate(tune):
@@ -567,7 +568,8 @@ def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None)
         "mean_unfinished": ss.mean_inflight, "mean_blocks_alive": ss.mean_blocks,
         "sm_occupancy_est": (ss.block_seconds - base.block_seconds) / wall / max(1, plan_slots),
         "vertices_mean": float(sizes.mean()), "vertices_p99": float(np.percentile(sizes, 99)),
-        "form": "FP32 values/matvec, FP64 reductions; continuous batching through a persistent kernel",
+        "form": "FP32 values/matvec, FP64 reductions; continuous batching through a persistent kernel" +
+                (f"; options {plan_opts}" if plan_opts else ""),
         "autotune": {"batch_threads": tuning.batch_threads, "sample_ms_512_256_128": [round(x, 2) for x in tuning.batch_ms],
                      "sample": "the 16 smallest pool graphs, repeated to fill the device"},
         "statuses": {str(k): int(v) for k, v in zip(*np.unique(stats_st, return_counts=True))},
@@ -866,6 +868,11 @@ def main():
         line["serving"] = extra_leg("serving", lambda: serving_leg(
             serve_pool, stream, dev, args.serve_rate, args.serve_seconds, seed=SERVE["seed"] + 7919 * rank,
             dist=dist))
+        # the same stream, shorter, with the finest-level LOBPCG refinement (the
+        # setting at which every result meets the 1e-5 lambda_2 gate)
+        line["serving_refined_lobpcg_1e-4"] = extra_leg("serving_refined", lambda: serving_leg(
+            serve_pool, stream, dev, args.serve_rate, args.serve_seconds / 2, seed=SERVE["seed"] + 7919 * rank,
+            dist=dist, refine=fiedler.FIEDLER_REFINE_LOBPCG, refine_tol=1e-4))
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
