@@ -228,9 +228,10 @@ size_t arena_estimate(int64_t n, int64_t nnz, size_t tsz, bool wf64, const fiedl
 
 size_t scratch_estimate(int64_t n, int64_t nnz, int nblocks, const fiedler_options &o) {
   // one level's scratch, all live at once: colouring (cround + 3 worklists +
-  // heavy list + resume positions), matching (cand + 3 worklists + heavy list), Galerkin (9 per-vertex / per-aggregate
-  // arrays, (J, slot) keys + FP64 weights per cross entry), colour histogram
-  double b = 24.0 * n + 20.0 * n + 4.0 * (n + 1) * 9 + 16.0 * nnz + 4.0 * fz::kMaxColors * nblocks +
+  // heavy list + resume positions), matching (two 8-byte pick buffers + 3
+  // worklists + heavy list), Galerkin (9 per-vertex / per-aggregate arrays,
+  // (J, slot) keys + FP64 weights per cross entry), colour histogram
+  double b = 24.0 * n + 32.0 * n + 4.0 * (n + 1) * 9 + 16.0 * nnz + 4.0 * fz::kMaxColors * nblocks +
              64.0 * 256.0 + (1 << 20);
   // Alg. 1's random-order greedy (hec_mode PAPER) keeps more per-vertex state
   // than the matching: heaviest neighbour, turn state, first claimant (key and

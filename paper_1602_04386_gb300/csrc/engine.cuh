@@ -60,6 +60,19 @@ FZD double uniform01(uint64_t seed, uint64_t k) {
   return (double)(sm64(seed, k) >> 11) * (1.0 / 9007199254740992.0);
 }
 
+// gpu-scope release / acquire primitives of the grid barrier
+FZD unsigned atom_add_release(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+FZD unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+FZD void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 FZD uint64_t gtime() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -815,20 +828,22 @@ struct Eng {
     __syncthreads();
     if (threadIdx.x == 0) {
       const unsigned add = bid == 0 ? 0x80000000u - (unsigned)(nb - 1) : 1u;
-      __threadfence();
-      const unsigned old = atomicAdd(&S->bar_word, add);
+      // the arrival releases the block's writes (ordered before it by the
+      // block barrier, release is cumulative); the load that sees the flip
+      // acquires every other block's
+      const unsigned old = atom_add_release(&S->bar_word, add);
       bool done = (((old + add) ^ old) & 0x80000000u) != 0u;
-      if (!done) {
-        volatile unsigned *bw = &S->bar_word;
+      if (done) {
+        fence_acquire();
+      } else {
         const uint64_t t0 = gtime();
         const uint64_t lim = S->opt.barrier_timeout_ns;
         unsigned spins = 0;
         while (!done) {
-          done = ((*bw ^ old) & 0x80000000u) != 0u;
+          done = ((ld_acquire(&S->bar_word) ^ old) & 0x80000000u) != 0u;
           if (!done && (++spins & 255u) == 0u && gtime() - t0 > lim) break;
         }
       }
-      __threadfence();
       if (!done) {
         fail(ST_ETIMEOUT);
         s_ok = 0;
@@ -1602,12 +1617,15 @@ struct Eng {
   }
 
   // ---- A2: heavy-edge matching by handshake rounds ---------------------------
-  // Phases alternate pick / match over block-owned worklists (as in colour()):
-  //   pick:  an active vertex points at its best unmatched neighbour under K;
-  //          vertices with a candidate go to the next list, the others have no
-  //          free neighbour now or later and drop out;
-  //   match: mutual candidates become pairs; the rest are active again.
-  // Stop after a pick that found no candidate, or a match that left nobody.
+  // Round k: every active vertex picks its best free neighbour under K; mutual
+  // picks become pairs; the others stay active, and a vertex left without a
+  // free neighbour drops out (the free set only shrinks, so it never gets one
+  // again).  Phase k settles the pairs of round k - 1 and makes the picks of
+  // round k in one pass over block-owned worklists, so one barrier separates
+  // two rounds.  The picks live in two buffers (round parity) as (round << 32 |
+  // vertex): during phase k a vertex u counts as taken iff it was matched
+  // before round k - 1 (mate) or its round-(k - 1) pick points at a vertex whose
+  // round-(k - 1) pick points back at u.  Stop after a phase with no pick.
   FZD bool match(int l) {
     cur_level = l;
     Level *L = &S->lv[l];
@@ -1616,11 +1634,12 @@ struct Eng {
     const int tie = S->opt.tie_rule;
     const W wl = wof(L);
     int *mate = (int *)aalloc(4ull * n);
-    int *cand = (int *)salloc(4ull * n);
+    unsigned long long *pick[2];
+    for (int k = 0; k < 2; k++) pick[k] = (unsigned long long *)salloc(8ull * n);
     int *list[3];
     for (int k = 0; k < 3; k++) list[k] = (int *)salloc(4ull * n);
     int *heavy = (int *)salloc(4ull * n);
-    if (!mate || !cand || !list[0] || !list[1] || !list[2] || !heavy) return false;
+    if (!mate || !pick[0] || !pick[1] || !list[0] || !list[1] || !list[2] || !heavy) return false;
     int lo, hi;
     chunk(n, lo, hi);
     int *s_cnt = sh_ints();
@@ -1635,8 +1654,14 @@ struct Eng {
     if (lead()) {
       S->wl_cnt[1] = 0;
       S->wl_cnt[2] = 0;
+      L->mate = mate;  // published by the barrier below; complete after the last phase's
     }
-    for (int v = tid; v < n; v += nthr) mate[v] = -1;
+    constexpr unsigned long long kNoPick = ~0ull;  // round tag 2^32 - 1: never current
+    for (int v = tid; v < n; v += nthr) {
+      mate[v] = -1;
+      pick[0][v] = kNoPick;
+      pick[1][v] = kNoPick;
+    }
     if (!sync_p()) return false;
     int rounds = 0;
     long long visits = 0;
@@ -1644,74 +1669,85 @@ struct Eng {
       const int cur = ph % 3, nxt = (ph + 1) % 3, clr = (ph + 2) % 3;
       if (lead() && ph > 0) S->wl_cnt[clr] = 0;
       const int cnt = s_cnt[cur];
-      if ((ph & 1) == 0) {  // pick
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-          const int v = ph == 0 ? lo + q : list[cur][lo + q];
-          if (ph > 0 && mate[cand[v]] < 0) {
+      const unsigned long long *pp = pick[(ph + 1) & 1];  // round ph - 1
+      unsigned long long *pn = pick[ph & 1];              // round ph
+      const unsigned long long tprev = (unsigned long long)(unsigned)(ph - 1) << 32;
+      const unsigned long long tcur = (unsigned long long)(unsigned)ph << 32;
+      auto taken = [&](int u) {
+        if (ph == 0) return false;
+        if (mate[u] >= 0) return true;
+        const unsigned long long a = pp[u];
+        if ((a >> 32) != (tprev >> 32)) return false;
+        return pp[(unsigned)a] == (tprev | (unsigned)u);
+      };
+      for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int v = ph == 0 ? lo + q : list[cur][lo + q];
+        if (ph > 0) {
+          // v picked in round ph - 1 (that is why it is on the list)
+          const int c = (int)(unsigned)pp[v];
+          if (pp[c] == (tprev | (unsigned)v)) {  // a pair of round ph - 1
+            mate[v] = c;
+            continue;
+          }
+          if (!taken(c)) {
             // the best free neighbour of the last pick is still free, and the
             // free set only shrinks, so it is still the best: no rescan
+            pn[v] = tcur | (unsigned)c;
             list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
             continue;
-          }
-          if (rp[v + 1] - rp[v] >= kHeavyDeg) {  // to the warps
-            hl[atomicAdd(&hc[1], 1)] = v;
-            continue;
-          }
-          Best b;
-          best_init(b);
-          for (int e = rp[v]; e < rp[v + 1]; e++) {
-            const int u = ci[e];
-            if (ph > 0 && mate[u] >= 0) continue;
-            const uint64_t wk = wl.key(e);
-            if (best_beats(b, wk, v, u, tie)) best_set(b, wk, v, u);
-          }
-          if (b.v >= 0) {
-            cand[v] = b.v;
-            list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
           }
         }
-        __syncthreads();
-        // heavy vertices: one warp each, lanes over the neighbours, then the
-        // warp's best under the same total order (unique, so the merge order
-        // does not matter)
-        const int nh = hc[1];
-        const int lane = threadIdx.x & 31;
-        const int mean = L->nnz / (n > 0 ? n : 1);
-        with_group<GRID>(mean < 128 ? 8 : mean < 512 ? 16 : 32, [&](auto gs) {
-          constexpr int G = decltype(gs)::value, GW = 32 / G;
-          const int gl = lane & (G - 1), gi = lane / G;
-          for (int kb = (threadIdx.x >> 5) * GW; kb < nh; kb += (blockDim.x >> 5) * GW) {
-            const int k = kb + gi;
-            const int v = k < nh ? hl[k] : 0;
-            Best b;
-            best_init(b);
-            b.wk = 0;
-            if (k < nh)
-              for (int e = rp[v] + gl; e < rp[v + 1]; e += G) {
-                const int u = ci[e];
-                if (ph > 0 && mate[u] >= 0) continue;
-                const uint64_t wk = wl.key(e);
-                if (best_beats(b, wk, v, u, tie)) best_set(b, wk, v, u);
-              }
-            for (int o = G >> 1; o >= 1; o >>= 1) {
-              const uint64_t owk = __shfl_xor_sync(0xffffffffu, b.wk, o);
-              const int ov = __shfl_xor_sync(0xffffffffu, b.v, o);
-              if (ov >= 0 && best_beats(b, owk, v, ov, tie)) best_set(b, owk, v, ov);
-            }
-            if (k < nh && gl == 0 && b.v >= 0) {
-              cand[v] = b.v;
-              list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
-            }
-          }
-        });
-      } else {  // match
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-          const int v = list[cur][lo + q];
-          const int c = cand[v];
-          if (cand[c] == v) mate[v] = c;
-          else list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
+        if (rp[v + 1] - rp[v] >= kHeavyDeg) {  // to the warps
+          hl[atomicAdd(&hc[1], 1)] = v;
+          continue;
+        }
+        Best b;
+        best_init(b);
+        for (int e = rp[v]; e < rp[v + 1]; e++) {
+          const int u = ci[e];
+          if (taken(u)) continue;
+          const uint64_t wk = wl.key(e);
+          if (best_beats(b, wk, v, u, tie)) best_set(b, wk, v, u);
+        }
+        if (b.v >= 0) {
+          pn[v] = tcur | (unsigned)b.v;
+          list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
         }
       }
+      __syncthreads();
+      // heavy vertices: one warp each, lanes over the neighbours, then the
+      // warp's best under the same total order (unique, so the merge order
+      // does not matter)
+      const int nh = hc[1];
+      const int lane = threadIdx.x & 31;
+      const int mean = L->nnz / (n > 0 ? n : 1);
+      with_group<GRID>(mean < 128 ? 8 : mean < 512 ? 16 : 32, [&](auto gs) {
+        constexpr int G = decltype(gs)::value, GW = 32 / G;
+        const int gl = lane & (G - 1), gi = lane / G;
+        for (int kb = (threadIdx.x >> 5) * GW; kb < nh; kb += (blockDim.x >> 5) * GW) {
+          const int k = kb + gi;
+          const int v = k < nh ? hl[k] : 0;
+          Best b;
+          best_init(b);
+          b.wk = 0;
+          if (k < nh)
+            for (int e = rp[v] + gl; e < rp[v + 1]; e += G) {
+              const int u = ci[e];
+              if (taken(u)) continue;
+              const uint64_t wk = wl.key(e);
+              if (best_beats(b, wk, v, u, tie)) best_set(b, wk, v, u);
+            }
+          for (int o = G >> 1; o >= 1; o >>= 1) {
+            const uint64_t owk = __shfl_xor_sync(0xffffffffu, b.wk, o);
+            const int ov = __shfl_xor_sync(0xffffffffu, b.v, o);
+            if (ov >= 0 && best_beats(b, owk, v, ov, tie)) best_set(b, owk, v, ov);
+          }
+          if (k < nh && gl == 0 && b.v >= 0) {
+            pn[v] = tcur | (unsigned)b.v;
+            list[nxt][lo + atomicAdd(&s_cnt[nxt], 1)] = v;
+          }
+        }
+      });
       __syncthreads();
       if (threadIdx.x == 0) {
         if (s_cnt[nxt]) atomicAdd(&S->wl_cnt[nxt], s_cnt[nxt]);
@@ -1720,20 +1756,11 @@ struct Eng {
       }
       visits += cnt;
       if (!sync_p()) return false;
-      const int total = wl_read(nxt);
-      if ((ph & 1) == 0) {
-        if (total == 0) break;
-        rounds++;
-      } else if (total == 0) {
-        break;
-      }
+      if (wl_read(nxt) == 0) break;  // no pick: the last pairs are settled
+      rounds++;
     }
-    if (lead()) {
-      L->mate = mate;
-      L->match_rounds = rounds;
-    }
-    if (!sync_p()) return false;
-    FZ_MARK(PH_MATCH, 4.0 * n + (double)visits * nb * (8.0 + 4.0 * 4 + (L->w64 ? 8.0 : 4.0) * 4));
+    if (lead()) L->match_rounds = rounds;
+    FZ_MARK(PH_MATCH, 20.0 * n + (double)visits * nb * (8.0 + 4.0 * 4 + 8.0 * 2 + (L->w64 ? 8.0 : 4.0) * 4));
     return true;
   }
 

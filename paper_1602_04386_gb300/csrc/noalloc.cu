@@ -50,7 +50,7 @@ size_t round256(size_t b) { return (b + 255u) & ~(size_t)255u; }
 
 // per-level scratch bound (every level is at most as large as the fine one)
 size_t scratch_bytes(int64_t n, int64_t nnz, int hec_mode) {
-  return round256((size_t)(44.0 * n + 4.0 * (n + 1) * 9 + 16.0 * nnz + 4.0 * fz::kMaxColors + 64.0 * 256.0 +
+  return round256((size_t)(56.0 * n + 4.0 * (n + 1) * 9 + 16.0 * nnz + 4.0 * fz::kMaxColors + 64.0 * 256.0 +
                            (hec_mode == FIEDLER_HEC_PAPER ? 44.0 * n + 8.0 * 256.0 : 0.0)));
 }
 
