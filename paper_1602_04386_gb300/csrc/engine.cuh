@@ -538,6 +538,39 @@ FZD void with_group(int g, F f) {
   }
 }
 
+// Per-thread sum of a sweep's row values for the FP64 reductions.  With
+// float iterates it is a float-float pair (hi + lo): every term goes in by
+// Knuth's TwoSum and every product of two floats by TwoProduct (its rounding
+// error from an FMA) before the TwoSum, so the pair holds the exact sum up
+// to the roundings of lo, about 2^-48 of it per term.  GB300 issues FP64 at
+// 1/56 of the FP32 rate with 64-cycle latency, and a row's four FP64 updates
+// were the power iteration's throughput limit.  The pair goes into the FP64
+// block sums.  With double iterates it is a plain double.
+template <class V>
+struct RowSum {
+  double d = 0.0;
+  FZD void add(V b) { d += (double)b; }
+  FZD void add_prod(V a, V b) { d += (double)a * (double)b; }
+  FZD double value() const { return d; }
+};
+template <>
+struct RowSum<float> {
+  float hi = 0.f, lo = 0.f;
+  FZD void add(float b) {
+    const float s = __fadd_rn(hi, b);
+    const float bb = __fsub_rn(s, hi);
+    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    hi = s;
+  }
+  FZD void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    add(p);
+    lo += e;
+  }
+  FZD double value() const { return (double)hi + (double)lo; }
+};
+
 // warp sum of one value by a fixed xor tree; result in every lane
 template <class V>
 FZD V warp_sum(V v) {
@@ -2571,13 +2604,14 @@ struct Eng {
     const VC muc = (VC)Cl->mu, scc = (VC)Cl->s;
     VF *x = (VF *)F->x;
     const int *sagg = F->sagg;
-    double acc[2] = {0.0, 0.0};
+    RowSum<VF> r0, r1;
     for (int k = tid; k < n; k += nthr) {
       const VF v = (VF)((xc[sagg[k]] - muc) * scc);
       x[k] = v;
-      acc[0] += (double)v;
-      acc[1] += (double)v * (double)v;
+      r0.add(v);
+      r1.add_prod(v, v);
     }
+    double acc[2] = {r0.value(), r1.value()};
     if (!grid_dsum<2>(acc)) return false;
     double mu, sc;
     if (!deflate_scalars(acc, n, mu, sc)) return false;
@@ -2626,6 +2660,7 @@ struct Eng {
     int sweeps = 0;
     for (int k = 0; k < nsweeps; k++) {
       double acc[2] = {0.0, 0.0};
+      RowSum<V> rs0, rs1;
       for (int c = 0; c < C; c++) {
         // class c: light rows [cs, ce), heavy rows [hs, he); a neighbour j is
         // already updated in this sweep iff its class is below c
@@ -2643,8 +2678,8 @@ struct Eng {
           }
           const V xi = num / dsum;
           B[i] = xi;
-          acc[0] += (double)xi;
-          acc[1] += (double)xi * (double)xi;
+          rs0.add(xi);
+          rs1.add_prod(xi, xi);
         }
         with_group<GRID>(hg, [&](auto gs) {  // heavy rows: a group of lanes each
           constexpr int G = decltype(gs)::value, GW = 32 / G;
@@ -2663,13 +2698,15 @@ struct Eng {
             if (gl == 0 && i < he) {
               const V xi = num / dsum;
               B[i] = xi;
-              acc[0] += (double)xi;
-              acc[1] += (double)xi * (double)xi;
+              rs0.add(xi);
+              rs1.add_prod(xi, xi);
             }
           }
         });
         if (c + 1 < C && !sync()) return false;
       }
+      acc[0] = rs0.value();
+      acc[1] = rs1.value();
       if (!grid_dsum<2>(acc)) return false;
       FZ_MARK(ph_gs, sweep_bytes);
       if (threadIdx.x == 0) {
@@ -2701,17 +2738,17 @@ struct Eng {
     for (int it = 1; it <= kmax; it++) {
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
       double acr[2] = {0.0, 0.0};
+      RowSum<V> ps0, ps1, ps2, ps3;
       auto row = [&](int i, V xi, V lx) {
         const V xh = (xi - muT) * sT;
         const V yi = sigT * xh - sT * lx;
         B[i] = yi;
-        const double yd = (double)yi, xd = (double)xh;
-        acc[0] += yd;
-        acc[1] += yd * yd;
-        acc[2] += yd * xd;
-        acc[3] += xd;
+        ps0.add(yi);
+        ps1.add_prod(yi, yi);
+        ps2.add_prod(yi, xh);
+        ps3.add(xh);
         if (resid) {
-          const double ld = (double)sT * (double)lx;
+          const double ld = (double)sT * (double)lx, xd = (double)xh;
           acr[0] += ld * ld;
           acr[1] += xd * ld;
         }
@@ -2740,6 +2777,10 @@ struct Eng {
           if (gl == 0 && i < n) row(i, xi, lx);
         }
       });
+      acc[0] = ps0.value();
+      acc[1] = ps1.value();
+      acc[2] = ps2.value();
+      acc[3] = ps3.value();
       if (!grid_dsum<4>(acc)) return false;
       if (resid && !grid_dsum<2>(acr)) return false;
       FZ_MARK(ph_pi, sweep_bytes);
