@@ -1,16 +1,16 @@
 // engine_batch128_f64.cu -- double batched and serving kernels with 128 threads per graph's block
-// (4 graph(s) resident per SM); one translation unit per variant so that
+// (8 graphs resident per SM); one translation unit per variant so that
 // they compile in parallel.
 #include "engine.cuh"
 #include "kernels.h"
 
 namespace fz {
 
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 8)
     fz_batch128_f64(State *states, int count, int *next, char *scratch, unsigned long long slot_bytes) {
   batch_entry<double>(states, count, next, scratch, slot_bytes);
 }
-__global__ void __launch_bounds__(128, 4) fz_serve128_f64(ServeRing *ring, ServeDone *fin,
+__global__ void __launch_bounds__(128, 8) fz_serve128_f64(ServeRing *ring, ServeDone *fin,
                                                               unsigned long long base) {
   serve_entry<double>(ring, fin, base);
 }

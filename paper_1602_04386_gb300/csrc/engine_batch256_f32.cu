@@ -1,16 +1,16 @@
 // engine_batch256_f32.cu -- float batched and serving kernels with 256 threads per graph's block
-// (2 graph(s) resident per SM); one translation unit per variant so that
+// (4 graphs resident per SM); one translation unit per variant so that
 // they compile in parallel.
 #include "engine.cuh"
 #include "kernels.h"
 
 namespace fz {
 
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 4)
     fz_batch256_f32(State *states, int count, int *next, char *scratch, unsigned long long slot_bytes) {
   batch_entry<float>(states, count, next, scratch, slot_bytes);
 }
-__global__ void __launch_bounds__(256, 2) fz_serve256_f32(ServeRing *ring, ServeDone *fin,
+__global__ void __launch_bounds__(256, 4) fz_serve256_f32(ServeRing *ring, ServeDone *fin,
                                                               unsigned long long base) {
   serve_entry<float>(ring, fin, base);
 }
