@@ -57,6 +57,8 @@ def assert_hierarchy_equal(p, ref):
             assert np.array_equal(a["mate"], b.mate), l
             assert np.array_equal(a["agg"], b.agg), l
             assert a["info"].nc == b.nc
+            # handshake rounds that made a pick (one barrier per round on the GPU)
+            assert a["info"].match_rounds == b.match_rounds, l
 
 
 def assert_residual_ortho(r, ref, precision, sigma):
