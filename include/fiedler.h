@@ -127,12 +127,14 @@ typedef struct {
   int lanczos_basis;         /* FIEDLER_REFINE_LANCZOS: basis vectors per restart cycle, 4..64 */
   int hec_mode;              /* FIEDLER_HEC_DOMINANT (default) or FIEDLER_HEC_PAPER */
   int refine_precond;        /* FIEDLER_PRECOND_VCYCLE (default) or FIEDLER_PRECOND_DEGREE */
-  int lane_sms;              /* serving form (a project addition): SMs whose block slots the
-                                serving kernel leaves to a lane for large graphs, which solves
-                                them one at a time with the cooperative grid-wide kernels on
-                                that many SMs (2 blocks per SM); 0 = no lane (default), at most
-                                half the device's SMs */
+  int lane_sms;              /* serving and batched forms (a project addition): SMs whose block
+                                slots the one-block kernels leave to a lane for large graphs,
+                                solved with the cooperative grid-wide kernels (2 blocks per SM);
+                                0 = no lane (default), at most half the device's SMs */
   int lane_min_n;            /* graphs with at least this many vertices take the lane (if any) */
+  int lane_slots;            /* serving form: large tickets solved at once, each on
+                                lane_sms / lane_slots SMs (the batched form runs its large graphs
+                                one after another on all lane_sms); 1..lane_sms, default 1 */
 } fiedler_options;
 
 typedef struct {
@@ -173,7 +175,7 @@ typedef struct fiedler_plan fiedler_plan;
  * hbm_budget_bytes 0 (16 GiB), max_batch 1024, queue_budget_bytes 0 (8 GiB),
  * batch_threads 0, refine NONE, refine_max_iters 5000, refine_tol 1e-4,
  * lanczos_basis 24, hec_mode DOMINANT, refine_precond VCYCLE, lane_sms 0,
- * lane_min_n 200000. */
+ * lane_min_n 200000, lane_slots 1. */
 void fiedler_options_default(fiedler_options *opts);
 
 /* Creates a plan on the current CUDA device.  opts may be NULL (defaults);

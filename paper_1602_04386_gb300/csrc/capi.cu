@@ -148,18 +148,34 @@ struct fiedler_plan {
   State *h_stage = nullptr;           // pinned staging of ticket states (max_batch of them)
   int stage_n = 0;
   std::deque<Ticket *> live;          // published, not yet finished (ring order)
-  // large-graph lane of the serving form: admitted large tickets wait in
-  // lane_q and run one at a time through the cooperative grid-wide kernels on
-  // lane_blocks blocks (lane_sms SMs) on the lane's own stream
-  struct Lane {
+  // large-graph lane: admitted large tickets of the serving form wait in q and
+  // run through the cooperative grid-wide kernels, lane_slots of them at once,
+  // each slot on its own stream with its own reduction partials on
+  // slot_blocks blocks (lane_sms / lane_slots SMs); the batched form runs its
+  // large graphs one after another on slot 0's stream on `blocks` blocks
+  // (lane_sms SMs)
+  struct LaneSlot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     fz::IRed *ipart = nullptr;
     double *dpart = nullptr;
-    int blocks[2] = {0, 0};  // [type] blocks of one lane launch
+    void **h_part = nullptr;  // pinned {ipart, dpart}: copied into a ticket's state before its launch
     Ticket *cur = nullptr;
+  };
+  struct Lane {
+    cudaStream_t stream = nullptr;  // slot 0's stream (null: no lane)
+    fz::IRed *ipart = nullptr;      // slot 0's partials
+    double *dpart = nullptr;
+    int blocks[2] = {0, 0};       // [type] blocks of one batched-form lane launch
+    int slot_blocks[2] = {0, 0};  // [type] blocks of one serving-lane launch
+    std::vector<LaneSlot> slots;
     std::deque<Ticket *> q;
     uint64_t solves = 0;
+    bool busy() const {
+      for (const LaneSlot &s : slots)
+        if (s.cur) return true;
+      return false;
+    }
   } lane;
   uint64_t n_launches = 0;
   // serving form
@@ -270,7 +286,7 @@ bool options_valid(const fiedler_options &o) {
            o.refine_max_iters < 0 || !(o.refine_tol > 0.0 && o.refine_tol < 1.0) || o.lanczos_basis < 4 ||
            o.lanczos_basis > fz::kMaxBasis || (o.hec_mode != FIEDLER_HEC_DOMINANT && o.hec_mode != FIEDLER_HEC_PAPER) ||
            (o.refine_precond != FIEDLER_PRECOND_DEGREE && o.refine_precond != FIEDLER_PRECOND_VCYCLE) ||
-           o.lane_sms < 0 || o.lane_min_n < 2);
+           o.lane_sms < 0 || o.lane_min_n < 2 || o.lane_slots < 1 || (o.lane_sms > 0 && o.lane_slots > o.lane_sms));
 }
 
 void fill_opts(fz::Opts &o, const fiedler_options &u, int type) {
@@ -849,62 +865,69 @@ void worker_main(fiedler_plan *p) {
         p->q_cv.notify_all();
       }
     }
-    // 1b. the large-graph lane: its finished ticket, then the next one
-    if (p->lane.cur && cudaEventQuery(p->lane.ev) == cudaSuccess) {
-      progressed = true;
-      Ticket *t = p->lane.cur;
-      p->lane.cur = nullptr;
-      const bool ok = cudaMemcpyAsync(p->h_stage, t->dwork, sizeof(State), cudaMemcpyDeviceToHost,
-                                      p->lane.stream) == cudaSuccess &&
-                      cudaStreamSynchronize(p->lane.stream) == cudaSuccess;
-      const State *h = p->h_stage;
-      const auto now = std::chrono::steady_clock::now();
-      std::lock_guard<std::mutex> lk(p->q_mu);
-      cudaFreeAsync(t->dwork, p->lane.stream);
-      t->dwork = nullptr;
-      p->inflight_bytes -= t->footprint;
-      if (ok && (h->status == fz::ST_ARENA || h->status == fz::ST_SCRATCH) && t->scale < 8.0) {
-        t->scale *= 2.0;  // the hierarchy outgrew its estimate: run it again with more room
-        t->running = false;
-        p->queue.push_front(t->id);
-      } else {
-        if (ok) ticket_result(h, t);
-        else t->st = FIEDLER_ECUDA;
-        if (ok && (h->status == fz::ST_ARENA || h->status == fz::ST_SCRATCH)) t->st = FIEDLER_ENOMEM;
-        mark_done(p, t);
-        t->running = false;
-        p->n_completed++;
-        p->lane.solves++;
-        p->latencies_ms.push_back(std::chrono::duration<float, std::milli>(now - t->t_submit).count());
-      }
-      p->q_cv.notify_all();
-    }
-    if (!p->lane.cur && !p->lane.q.empty()) {
-      progressed = true;
-      Ticket *t = p->lane.q.front();
-      p->lane.q.pop_front();
-      const fz::KernelSet &K = p->ks[type];
-      const int nbl = p->lane.blocks[type];
-      void *args[] = {(void *)&t->dwork};
-      const bool ok =
-          cudaLaunchCooperativeKernel(K.grid_setup, dim3(nbl), dim3(fz::kGridThreads), args, 0, p->lane.stream) ==
-              cudaSuccess &&
-          cudaLaunchKernel(K.cta, dim3(1), dim3(fz::kCtaThreads), args, 0, p->lane.stream) == cudaSuccess &&
-          cudaLaunchCooperativeKernel(K.grid_solve, dim3(nbl), dim3(fz::kGridThreads), args, 0, p->lane.stream) ==
-              cudaSuccess &&
-          cudaEventRecord(p->lane.ev, p->lane.stream) == cudaSuccess;
-      if (ok) {
-        p->lane.cur = t;
-        p->n_launches += 3;
-      } else {
+    // 1b. the large-graph lane: each slot's finished ticket, then its next one
+    for (fiedler_plan::LaneSlot &sl : p->lane.slots) {
+      if (sl.cur && cudaEventQuery(sl.ev) == cudaSuccess) {
+        progressed = true;
+        Ticket *t = sl.cur;
+        sl.cur = nullptr;
+        State *hs = p->h_stage;  // read back and synchronised before the next slot's
+        const bool ok = cudaMemcpyAsync(hs, t->dwork, sizeof(State), cudaMemcpyDeviceToHost, sl.stream) ==
+                            cudaSuccess &&
+                        cudaStreamSynchronize(sl.stream) == cudaSuccess;
+        const State *h = hs;
+        const auto now = std::chrono::steady_clock::now();
         std::lock_guard<std::mutex> lk(p->q_mu);
-        cudaFreeAsync(t->dwork, p->lane.stream);
+        cudaFreeAsync(t->dwork, sl.stream);
         t->dwork = nullptr;
         p->inflight_bytes -= t->footprint;
-        t->st = FIEDLER_ECUDA;
-        mark_done(p, t);
-        t->running = false;
+        if (ok && (h->status == fz::ST_ARENA || h->status == fz::ST_SCRATCH) && t->scale < 8.0) {
+          t->scale *= 2.0;  // the hierarchy outgrew its estimate: run it again with more room
+          t->running = false;
+          p->queue.push_front(t->id);
+        } else {
+          if (ok) ticket_result(h, t);
+          else t->st = FIEDLER_ECUDA;
+          if (ok && (h->status == fz::ST_ARENA || h->status == fz::ST_SCRATCH)) t->st = FIEDLER_ENOMEM;
+          mark_done(p, t);
+          t->running = false;
+          p->n_completed++;
+          p->lane.solves++;
+          p->latencies_ms.push_back(std::chrono::duration<float, std::milli>(now - t->t_submit).count());
+        }
         p->q_cv.notify_all();
+      }
+      if (!sl.cur && !p->lane.q.empty()) {
+        progressed = true;
+        Ticket *t = p->lane.q.front();
+        p->lane.q.pop_front();
+        const fz::KernelSet &K = p->ks[type];
+        const int nbl = p->lane.slot_blocks[type];
+        void *args[] = {(void *)&t->dwork};
+        // the slot's reduction partials into the ticket's state, in stream order
+        // before its kernels (ipart and dpart are adjacent in State)
+        const bool ok =
+            cudaMemcpyAsync((char *)t->dwork + offsetof(State, ipart), sl.h_part, 2 * sizeof(void *),
+                            cudaMemcpyHostToDevice, sl.stream) == cudaSuccess &&
+            cudaLaunchCooperativeKernel(K.grid_setup, dim3(nbl), dim3(fz::kGridThreads), args, 0, sl.stream) ==
+                cudaSuccess &&
+            cudaLaunchKernel(K.cta, dim3(1), dim3(fz::kCtaThreads), args, 0, sl.stream) == cudaSuccess &&
+            cudaLaunchCooperativeKernel(K.grid_solve, dim3(nbl), dim3(fz::kGridThreads), args, 0, sl.stream) ==
+                cudaSuccess &&
+            cudaEventRecord(sl.ev, sl.stream) == cudaSuccess;
+        if (ok) {
+          sl.cur = t;
+          p->n_launches += 3;
+        } else {
+          std::lock_guard<std::mutex> lk(p->q_mu);
+          cudaFreeAsync(t->dwork, sl.stream);
+          t->dwork = nullptr;
+          p->inflight_bytes -= t->footprint;
+          t->st = FIEDLER_ECUDA;
+          mark_done(p, t);
+          t->running = false;
+          p->q_cv.notify_all();
+        }
       }
     }
     // 2. admissions
@@ -930,7 +953,7 @@ void worker_main(fiedler_plan *p) {
         t->lane = p->lane.stream && t->n >= p->opt.lane_min_n;
         t->learn = p->arena_factor();
         t->arena_b = r256((size_t)(arena_estimate(t->n, t->nnz, tsz, t->w_dtype == FIEDLER_W_F64, p->opt) * t->scale * t->learn));
-        t->scratch_b = r256((size_t)(scratch_estimate(t->n, t->nnz, t->lane ? p->lane.blocks[type] : 1, p->opt) *
+        t->scratch_b = r256((size_t)(scratch_estimate(t->n, t->nnz, t->lane ? p->lane.slot_blocks[type] : 1, p->opt) *
                                      t->scale));
         t->footprint = r256(sizeof(State)) + t->arena_b + t->scratch_b;
         const bool empty = p->inflight_bytes == 0 && adm.empty();
@@ -961,7 +984,8 @@ void worker_main(fiedler_plan *p) {
         }
         State *h = p->h_stage + staged++;
         fill_ticket_state(p, t, h, type, ab, sb);
-        if (t->lane) {  // the grid-wide engine on the large levels, with the lane's partials
+        if (t->lane) {  // the grid-wide engine on the large levels; the partials
+                        // are those of the slot that launches it (written then)
           h->opt.tail_max_n = p->opt.tail_max_n;
           h->opt.tail_max_nnz = p->opt.tail_max_nnz;
           h->ipart = p->lane.ipart;
@@ -1064,7 +1088,7 @@ void worker_main(fiedler_plan *p) {
     if (!progressed) {
       std::unique_lock<std::mutex> lk(p->q_mu);
       if (p->stop) break;
-      if (p->live.empty() && p->queue.empty() && !p->lane.cur && p->lane.q.empty())
+      if (p->live.empty() && p->queue.empty() && !p->lane.busy() && p->lane.q.empty())
         p->q_cv.wait(lk, [&] { return p->stop || !p->queue.empty(); });
       else p->q_cv.wait_for(lk, std::chrono::microseconds(50));
     }
@@ -1079,11 +1103,12 @@ void worker_main(fiedler_plan *p) {
     if (L.running) cudaEventSynchronize(L.ev);
     L.running = false;
   }
-  if (p->lane.cur) {
-    cudaEventSynchronize(p->lane.ev);
-    p->live.push_back(p->lane.cur);  // released below
-    p->lane.cur = nullptr;
-  }
+  for (fiedler_plan::LaneSlot &sl : p->lane.slots)
+    if (sl.cur) {
+      cudaEventSynchronize(sl.ev);
+      p->live.push_back(sl.cur);  // released below
+      sl.cur = nullptr;
+    }
   for (Ticket *t : p->lane.q) p->live.push_back(t);
   p->lane.q.clear();
   for (Ticket *t : p->live) {
@@ -1248,6 +1273,7 @@ void fiedler_options_default(fiedler_options *o) {
   o->refine_precond = FIEDLER_PRECOND_VCYCLE;
   o->lane_sms = 0;
   o->lane_min_n = 200000;
+  o->lane_slots = 1;
 }
 
 fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_stream, fiedler_plan **out) {
@@ -1302,15 +1328,27 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
   p->batch_var = o.batch_threads == 256 ? 1 : o.batch_threads == 128 ? 2 : 0;
   if (o.lane_sms > 0) {
     if (o.lane_sms > p->sms / 2) return fail(FIEDLER_EINVAL);
+    const int per_slot = o.lane_sms / o.lane_slots;
     for (int t = 0; t < 2; t++) {
-      const int bps = std::min(p->grid_blocks[t][0], p->grid_blocks[t][1]) / p->sms;
-      p->lane.blocks[t] = std::max(1, bps) * o.lane_sms;
+      const int bps = std::max(1, std::min(p->grid_blocks[t][0], p->grid_blocks[t][1]) / p->sms);
+      p->lane.blocks[t] = bps * o.lane_sms;
+      p->lane.slot_blocks[t] = bps * per_slot;
     }
-    if (cudaStreamCreateWithFlags(&p->lane.stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FIEDLER_ECUDA);
-    if (cudaEventCreateWithFlags(&p->lane.ev, cudaEventDisableTiming) != cudaSuccess) return fail(FIEDLER_ECUDA);
-    if (cudaMalloc(&p->lane.ipart, sizeof(fz::IRed) * 2 * fz::kMaxBlocks) != cudaSuccess) return fail(FIEDLER_ENOMEM);
-    if (cudaMalloc(&p->lane.dpart, sizeof(double) * 2 * fz::kMaxBlocks * fz::kDSum) != cudaSuccess)
-      return fail(FIEDLER_ENOMEM);
+    p->lane.slots.resize(o.lane_slots);
+    for (fiedler_plan::LaneSlot &sl : p->lane.slots) {
+      if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) return fail(FIEDLER_ECUDA);
+      if (cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) return fail(FIEDLER_ECUDA);
+      if (cudaMalloc(&sl.ipart, sizeof(fz::IRed) * 2 * fz::kMaxBlocks) != cudaSuccess) return fail(FIEDLER_ENOMEM);
+      if (cudaMalloc(&sl.dpart, sizeof(double) * 2 * fz::kMaxBlocks * fz::kDSum) != cudaSuccess)
+        return fail(FIEDLER_ENOMEM);
+      if (cudaHostAlloc((void **)&sl.h_part, 2 * sizeof(void *), cudaHostAllocDefault) != cudaSuccess)
+        return fail(FIEDLER_ENOMEM);
+      sl.h_part[0] = sl.ipart;
+      sl.h_part[1] = sl.dpart;
+    }
+    p->lane.stream = p->lane.slots[0].stream;
+    p->lane.ipart = p->lane.slots[0].ipart;
+    p->lane.dpart = p->lane.slots[0].dpart;
   }
   p->bsync.stream = p->stream;
   if (cudaEventCreateWithFlags(&p->bsync.done, cudaEventDisableTiming) != cudaSuccess) return fail(FIEDLER_ECUDA);
@@ -1802,13 +1840,16 @@ void fiedler_plan_destroy(fiedler_plan *p) {
   if (p->d_state) cudaFree(p->d_state);
   if (p->d_ipart) cudaFree(p->d_ipart);
   if (p->d_dpart) cudaFree(p->d_dpart);
-  if (p->lane.stream) {
-    cudaStreamSynchronize(p->lane.stream);
-    cudaStreamDestroy(p->lane.stream);
+  for (fiedler_plan::LaneSlot &sl : p->lane.slots) {
+    if (sl.stream) {
+      cudaStreamSynchronize(sl.stream);
+      cudaStreamDestroy(sl.stream);
+    }
+    if (sl.ev) cudaEventDestroy(sl.ev);
+    if (sl.ipart) cudaFree(sl.ipart);
+    if (sl.dpart) cudaFree(sl.dpart);
+    if (sl.h_part) cudaFreeHost(sl.h_part);
   }
-  if (p->lane.ev) cudaEventDestroy(p->lane.ev);
-  if (p->lane.ipart) cudaFree(p->lane.ipart);
-  if (p->lane.dpart) cudaFree(p->lane.dpart);
   if (p->h_state) cudaFreeHost(p->h_state);
   for (int i = 0; i < 10; i++)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);

@@ -86,6 +86,7 @@ class fiedler_options(C.Structure):
         ("refine_precond", C.c_int),
         ("lane_sms", C.c_int),
         ("lane_min_n", C.c_int),
+        ("lane_slots", C.c_int),
     ]
 
 

@@ -62,9 +62,12 @@ def test_lane_results_match_oracle(precision, tol):
         assert np.abs(r.x - ref.x(g.n)).max() <= 1e-8
 
 
-def test_serving_with_lane_alone_equals_mix():
+@pytest.mark.parametrize("slots", [1, 2])
+def test_serving_with_lane_alone_equals_mix(slots):
+    """Large tickets run lane_slots at a time, each slot on its own stream and
+    reduction partials: results are the same bits alone and in the mix."""
     gs = mix()
-    with fiedler.Plan(**LANE) as p:
+    with fiedler.Plan(lane_slots=slots, **LANE) as p:
         alone = []
         for g in gs:
             t = p.submit(g)
@@ -76,6 +79,13 @@ def test_serving_with_lane_alone_equals_mix():
             st, r = p.poll(t, -1, n=g.n)
             assert st == fiedler.FIEDLER_OK, g.name
             assert r.lambda2 == a.lambda2 and np.array_equal(r.x, a.x), g.name
+
+
+def test_lane_slot_options_checked():
+    with pytest.raises(fiedler.FiedlerError):
+        fiedler.Plan(lane_sms=8, lane_slots=9)
+    with pytest.raises(fiedler.FiedlerError):
+        fiedler.Plan(lane_sms=8, lane_slots=0)
 
 
 def test_lane_refined_batch_matches_fp64():
