@@ -440,6 +440,16 @@ def configs_leg(stream, dev, steps=5, warmup=2):
 
 
 SERVE = dict(rate=2000.0, seconds=3.0, pool=24, nmin=1e3, nmax=2e6, seed=inputs.BASE_SEED + 5)
+# the large-graph lane: half the SMs, four tickets at once, graphs of 1e5 vertices and more
+SERVE_LANE = dict(lane_sms=76, lane_slots=4, lane_min_n=100000)
+
+
+def lane_opts(dev):
+    """SERVE_LANE scaled to the device: at most half its SMs go to the lane."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    lane = min(SERVE_LANE["lane_sms"], sms // 2)
+    return dict(SERVE_LANE, lane_sms=lane, lane_slots=max(1, min(SERVE_LANE["lane_slots"], lane)))
 
 
 def serving_leg(pool, stream, dev, rate, seconds, seed=SERVE["seed"], dist=None, **plan_opts):
@@ -867,12 +877,12 @@ def main():
     if serve_pool is not None:
         line["serving"] = extra_leg("serving", lambda: serving_leg(
             serve_pool, stream, dev, args.serve_rate, args.serve_seconds, seed=SERVE["seed"] + 7919 * rank,
-            dist=dist))
+            dist=dist, **lane_opts(dev)))
         # the same stream, shorter, with the finest-level LOBPCG refinement (the
         # setting at which every result meets the 1e-5 lambda_2 gate)
         line["serving_refined_lobpcg_1e-4"] = extra_leg("serving_refined", lambda: serving_leg(
             serve_pool, stream, dev, args.serve_rate, args.serve_seconds / 2, seed=SERVE["seed"] + 7919 * rank,
-            dist=dist, refine=fiedler.FIEDLER_REFINE_LOBPCG, refine_tol=1e-4))
+            dist=dist, refine=fiedler.FIEDLER_REFINE_LOBPCG, refine_tol=1e-4, **lane_opts(dev)))
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
