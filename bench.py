@@ -440,15 +440,15 @@ def configs_leg(stream, dev, steps=5, warmup=2):
 
 
 SERVE = dict(rate=2000.0, seconds=3.0, pool=24, nmin=1e3, nmax=2e6, seed=inputs.BASE_SEED + 5)
-# the large-graph lane: half the SMs, four tickets at once, graphs of 1e5 vertices and more
-SERVE_LANE = dict(lane_sms=76, lane_slots=4, lane_min_n=100000)
+# the large-graph lane: 96 of 152 SMs, six tickets at once, graphs of 1e5 vertices and more
+SERVE_LANE = dict(lane_sms=96, lane_slots=6, lane_min_n=100000)
 
 
 def lane_opts(dev):
-    """SERVE_LANE scaled to the device: at most half its SMs go to the lane."""
+    """SERVE_LANE on this device: the lane leaves 16 SMs or more to the one-block kernels."""
     import torch
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    lane = min(SERVE_LANE["lane_sms"], sms // 2)
+    lane = max(0, min(SERVE_LANE["lane_sms"], sms - 16))
     return dict(SERVE_LANE, lane_sms=lane, lane_slots=max(1, min(SERVE_LANE["lane_slots"], lane)))
 
 

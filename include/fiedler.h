@@ -130,7 +130,7 @@ typedef struct {
   int lane_sms;              /* serving and batched forms (a project addition): SMs whose block
                                 slots the one-block kernels leave to a lane for large graphs,
                                 solved with the cooperative grid-wide kernels (2 blocks per SM);
-                                0 = no lane (default), at most half the device's SMs */
+                                0 = no lane (default), at most the device's SMs minus 16 */
   int lane_min_n;            /* graphs with at least this many vertices take the lane (if any) */
   int lane_slots;            /* serving form: large tickets solved at once, each on
                                 lane_sms / lane_slots SMs (the batched form runs its large graphs

@@ -136,6 +136,7 @@ struct fiedler_plan {
   unsigned long long published = 0;
   static constexpr unsigned long long kIdleNs = 20000000ull;  // a serving block idle this long leaves
   static constexpr int kReserveSms = 2;  // SMs whose block slots serving launches leave free
+  static constexpr int kLaneFreeSms = 16;  // SMs a lane (lane_sms) leaves to the one-block kernels at least
   struct ServeLaunch {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
@@ -1327,7 +1328,8 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
     }
   p->batch_var = o.batch_threads == 256 ? 1 : o.batch_threads == 128 ? 2 : 0;
   if (o.lane_sms > 0) {
-    if (o.lane_sms > p->sms / 2) return fail(FIEDLER_EINVAL);
+    // the one-block kernels keep the block slots of at least kLaneFreeSms SMs
+    if (o.lane_sms > p->sms - fiedler_plan::kLaneFreeSms) return fail(FIEDLER_EINVAL);
     const int per_slot = o.lane_sms / o.lane_slots;
     for (int t = 0; t < 2; t++) {
       const int bps = std::max(1, std::min(p->grid_blocks[t][0], p->grid_blocks[t][1]) / p->sms);

@@ -86,6 +86,11 @@ def test_lane_slot_options_checked():
         fiedler.Plan(lane_sms=8, lane_slots=9)
     with pytest.raises(fiedler.FiedlerError):
         fiedler.Plan(lane_sms=8, lane_slots=0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    with pytest.raises(fiedler.FiedlerError):  # the one-block kernels keep 16 SMs
+        fiedler.Plan(lane_sms=sms - 15)
+    with fiedler.Plan(lane_sms=sms - 16, lane_slots=4):
+        pass
 
 
 def test_lane_refined_batch_matches_fp64():
