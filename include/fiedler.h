@@ -132,9 +132,8 @@ typedef struct {
                                 solved with the cooperative grid-wide kernels (2 blocks per SM);
                                 0 = no lane (default), at most the device's SMs minus 16 */
   int lane_min_n;            /* graphs with at least this many vertices take the lane (if any) */
-  int lane_slots;            /* serving form: large tickets solved at once, each on
-                                lane_sms / lane_slots SMs (the batched form runs its large graphs
-                                one after another on all lane_sms); 1..lane_sms, default 1 */
+  int lane_slots;            /* large graphs solved at once on the lane, each on
+                                lane_sms / lane_slots SMs; 1..lane_sms, default 1 */
 } fiedler_options;
 
 typedef struct {

@@ -152,9 +152,8 @@ struct fiedler_plan {
   // large-graph lane: admitted large tickets of the serving form wait in q and
   // run through the cooperative grid-wide kernels, lane_slots of them at once,
   // each slot on its own stream with its own reduction partials on
-  // slot_blocks blocks (lane_sms / lane_slots SMs); the batched form runs its
-  // large graphs one after another on slot 0's stream on `blocks` blocks
-  // (lane_sms SMs)
+  // slot_blocks blocks (lane_sms / lane_slots SMs); the batched form spreads
+  // its large graphs over the same slots
   struct LaneSlot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
@@ -167,8 +166,7 @@ struct fiedler_plan {
     cudaStream_t stream = nullptr;  // slot 0's stream (null: no lane)
     fz::IRed *ipart = nullptr;      // slot 0's partials
     double *dpart = nullptr;
-    int blocks[2] = {0, 0};       // [type] blocks of one batched-form lane launch
-    int slot_blocks[2] = {0, 0};  // [type] blocks of one serving-lane launch
+    int slot_blocks[2] = {0, 0};  // [type] blocks of one lane launch
     std::vector<LaneSlot> slots;
     std::deque<Ticket *> q;
     uint64_t solves = 0;
@@ -1333,7 +1331,6 @@ fiedler_status fiedler_plan_create(const fiedler_options *opts, void *cuda_strea
     const int per_slot = o.lane_sms / o.lane_slots;
     for (int t = 0; t < 2; t++) {
       const int bps = std::max(1, std::min(p->grid_blocks[t][0], p->grid_blocks[t][1]) / p->sms);
-      p->lane.blocks[t] = bps * o.lane_sms;
       p->lane.slot_blocks[t] = bps * per_slot;
     }
     p->lane.slots.resize(o.lane_slots);
@@ -1471,12 +1468,13 @@ fiedler_status fiedler_batch_submit(fiedler_plan *p, const fiedler_graph *g, uin
 
 namespace {
 
-// The large graphs of a batched call, solved one after another on the lane's
-// stream with the cooperative grid-wide kernels on lane_sms SMs (2 blocks per
-// SM) while the batched kernel, launched with those SMs left free, runs the
-// others.  lane_queue queues them (its device memory stays allocated until
-// lane_finish), lane_finish waits, fills the results and reruns any graph
-// whose hierarchy outgrew its arena or scratch.
+// The large graphs of a batched call, solved by the cooperative grid-wide
+// kernels on the lane's slots (graph i on slot i mod lane_slots, one after
+// another within a slot, each slot on lane_sms / lane_slots SMs with its own
+// stream and reduction partials) while the batched kernel, launched with the
+// lane's SMs left free, runs the others.  lane_queue queues them (their device
+// memory stays allocated until lane_finish), lane_finish waits, fills the
+// results and reruns any graph whose hierarchy outgrew its arena or scratch.
 struct LaneBatch {
   std::vector<BatchItem> items;
   State *hs = nullptr;  // pinned: the state copies must not block the host
@@ -1489,7 +1487,8 @@ struct LaneBatch {
 
 fiedler_status lane_queue(fiedler_plan *p, LaneBatch &lb, int type) {
   const size_t tsz = type == 0 ? 8 : 4;
-  const int nbl = p->lane.blocks[type];
+  const int nbl = p->lane.slot_blocks[type];
+  const size_t nsl = p->lane.slots.size();
   std::vector<size_t> off(lb.items.size());
   size_t total = 0;
   for (size_t i = 0; i < lb.items.size(); i++) {
@@ -1504,12 +1503,20 @@ fiedler_status lane_queue(fiedler_plan *p, LaneBatch &lb, int type) {
     if (it.user_x && !it.user_x_dev) total += r256(8 * (size_t)it.n);
   }
   CK(cudaMallocAsync((void **)&lb.d, std::max<size_t>(total, 256), p->lane.stream));
+  if (nsl > 1) {  // the other slots start after the allocation
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventRecord(e, p->lane.stream));
+    for (size_t k = 1; k < nsl; k++) CK(cudaStreamWaitEvent(p->lane.slots[k].stream, e, 0));
+    cudaEventDestroy(e);
+  }
   if (lb.hs) cudaFreeHost(lb.hs);
   lb.hs = nullptr;
   CK(cudaMallocHost((void **)&lb.hs, sizeof(State) * lb.items.size()));
   const fz::KernelSet &K = p->ks[type];
   for (size_t i = 0; i < lb.items.size(); i++) {
     BatchItem &it = lb.items[i];
+    const fiedler_plan::LaneSlot &sl = p->lane.slots[i % nsl];
     char *base = lb.d + off[i];
     State *h = &lb.hs[i];
     memset(h, 0, sizeof(State));
@@ -1529,11 +1536,11 @@ fiedler_status lane_queue(fiedler_plan *p, LaneBatch &lb, int type) {
     h->in_w_f64 = it.wf64;
     if (it.host_in) {
       const size_t rb = r256(4 * (size_t)(it.n + 1)), cb = r256(4 * (size_t)std::max<int64_t>(it.nnz, 1));
-      CK(cudaMemcpyAsync(q, it.rp, 4 * (size_t)(it.n + 1), cudaMemcpyHostToDevice, p->lane.stream));
+      CK(cudaMemcpyAsync(q, it.rp, 4 * (size_t)(it.n + 1), cudaMemcpyHostToDevice, sl.stream));
       if (it.nnz > 0) {
-        CK(cudaMemcpyAsync(q + rb, it.ci, 4 * (size_t)it.nnz, cudaMemcpyHostToDevice, p->lane.stream));
+        CK(cudaMemcpyAsync(q + rb, it.ci, 4 * (size_t)it.nnz, cudaMemcpyHostToDevice, sl.stream));
         CK(cudaMemcpyAsync(q + rb + cb, it.w, (it.wf64 ? 8 : 4) * (size_t)it.nnz, cudaMemcpyHostToDevice,
-                           p->lane.stream));
+                           sl.stream));
       }
       h->in_rowptr = (const int *)q;
       h->in_col = (const int *)(q + rb);
@@ -1542,14 +1549,14 @@ fiedler_status lane_queue(fiedler_plan *p, LaneBatch &lb, int type) {
     }
     h->xout = it.user_x ? (it.user_x_dev ? it.user_x : (double *)q) : nullptr;
     it.x_off = (size_t)(q - lb.d);
-    h->ipart = p->lane.ipart;
-    h->dpart = p->lane.dpart;
-    CK(cudaMemcpyAsync(base, h, sizeof(State), cudaMemcpyHostToDevice, p->lane.stream));
+    h->ipart = sl.ipart;
+    h->dpart = sl.dpart;
+    CK(cudaMemcpyAsync(base, h, sizeof(State), cudaMemcpyHostToDevice, sl.stream));
     void *args[] = {(void *)&base};
-    CK(cudaLaunchCooperativeKernel(K.grid_setup, dim3(nbl), dim3(fz::kGridThreads), args, 0, p->lane.stream));
-    CK(cudaLaunchKernel(K.cta, dim3(1), dim3(fz::kCtaThreads), args, 0, p->lane.stream));
-    CK(cudaLaunchCooperativeKernel(K.grid_solve, dim3(nbl), dim3(fz::kGridThreads), args, 0, p->lane.stream));
-    CK(cudaMemcpyAsync(h, base, sizeof(State), cudaMemcpyDeviceToHost, p->lane.stream));
+    CK(cudaLaunchCooperativeKernel(K.grid_setup, dim3(nbl), dim3(fz::kGridThreads), args, 0, sl.stream));
+    CK(cudaLaunchKernel(K.cta, dim3(1), dim3(fz::kCtaThreads), args, 0, sl.stream));
+    CK(cudaLaunchCooperativeKernel(K.grid_solve, dim3(nbl), dim3(fz::kGridThreads), args, 0, sl.stream));
+    CK(cudaMemcpyAsync(h, base, sizeof(State), cudaMemcpyDeviceToHost, sl.stream));
     it.in_off = off[i];
   }
   return FIEDLER_OK;
@@ -1557,7 +1564,7 @@ fiedler_status lane_queue(fiedler_plan *p, LaneBatch &lb, int type) {
 
 fiedler_status lane_finish(fiedler_plan *p, LaneBatch &lb, int type) {
   for (int attempt = 0;; attempt++) {
-    CK(cudaStreamSynchronize(p->lane.stream));
+    for (const fiedler_plan::LaneSlot &sl : p->lane.slots) CK(cudaStreamSynchronize(sl.stream));
     std::vector<BatchItem> again;
     for (size_t i = 0; i < lb.items.size(); i++) {
       BatchItem &it = lb.items[i];
@@ -1645,7 +1652,7 @@ fiedler_status fiedler_solve_batch(fiedler_plan *p, const fiedler_graph *graphs,
       cudaEvent_t e = nullptr;
       CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       CK(cudaEventRecord(e, p->stream));  // inputs the caller queued on the plan's stream
-      CK(cudaStreamWaitEvent(p->lane.stream, e, 0));
+      for (const fiedler_plan::LaneSlot &sl : p->lane.slots) CK(cudaStreamWaitEvent(sl.stream, e, 0));
       cudaEventDestroy(e);
       fiedler_status st = lane_queue(p, lb, c.type);
       if (st != FIEDLER_OK) return st;
