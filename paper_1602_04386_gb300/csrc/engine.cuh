@@ -322,7 +322,8 @@ FZD double tri_smallest(const double *al, const double *be, int k, double *s, do
 // ---------------------------------------------------------------------------
 // shared storage: a static __shared__ declared in a function is one allocation
 // per kernel
-constexpr int kShSort = 2048;  // u64 words of the raw buffer (16 KB); also kWarpSeg per warp
+constexpr int kShSort = 2560;  // u64 words of the raw buffer (20 KB): block sums, Gram and
+                                // basis dots of up to 32 warps, sorts (kWarpSeg per warp)
 constexpr int kSmallSeg = 32;  // segments up to this length are sorted by one thread
 constexpr int kWarpSeg = 128;  // longer ones up to this length by one warp (in shared memory)
 constexpr int kWarpSegG = 2048;  // longer ones up to this length by one warp in place (global memory)
@@ -335,11 +336,11 @@ FZD uint64_t *sh_raw() {
   return raw;
 }
 FZD int *sh_list() {
-  __shared__ int list[kCtaThreads];
+  __shared__ int list[kMaxThreads];
   return list;
 }
 FZD int *sh_list2() {
-  __shared__ int list[kCtaThreads];
+  __shared__ int list[kMaxThreads];
   return list;
 }
 FZD int *sh_ints() {
@@ -682,11 +683,12 @@ FZD void warp_bitonic(K *a, int len) {
 // the lanes' global accesses too)
 template <class K>
 FZD void warp_sort(K *g, int len) {
-  if (len > kWarpSeg) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // warps whose slice would lie beyond the raw buffer sort in place (the same order)
+  if (len > kWarpSeg || (w + 1) * kWarpSeg * (int)sizeof(K) > kShSort * (int)sizeof(uint64_t)) {
     warp_bitonic(g, len);
     return;
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   K *s = reinterpret_cast<K *>(sh_raw()) + w * kWarpSeg;
   for (int i = lane; i < len; i += 32) s[i] = g[i];
   __syncwarp();

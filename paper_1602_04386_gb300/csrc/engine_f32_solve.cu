@@ -6,7 +6,7 @@
 
 namespace fz {
 
-__global__ void __launch_bounds__(kGridThreads, 2) fz_grid_solve_f32(State *S) { engine_entry<float, true>(S, 2); }
+__global__ void __launch_bounds__(kGridThreads, 1) fz_grid_solve_f32(State *S) { engine_entry<float, true>(S, 2); }
 
 void grid_solve_kernel_f32(KernelSet *k) { k->grid_solve = (const void *)fz_grid_solve_f32; }
 

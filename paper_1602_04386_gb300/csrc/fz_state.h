@@ -11,7 +11,8 @@ constexpr int kMaxLevels = 32;
 constexpr int kMaxBlocks = 2048;   // grid-wide kernel blocks (partials buffer size)
 constexpr int kMaxColors = 1024;   // colour classes per level supported by the reorder
 constexpr int kCtaThreads = 512;   // one-block kernel
-constexpr int kGridThreads = 512;  // grid-wide kernel block size
+constexpr int kMaxThreads = 1024;  // largest block of any engine kernel (shared worklists)
+constexpr int kGridThreads = 1024;  // grid-wide kernel block size (one block per SM)
 // tiny levels (n <= kTinyN and nnz <= kTinyNnz): always in the one-block
 // engine, smoothed by one warp, values in FP64 in both forms
 constexpr int kTinyN = 256;
